@@ -1,0 +1,284 @@
+"""Pins of the oracle's physical model (arXiv 2203.00879, Sec. 2 and Sec. 4)
+against closed forms, a symbolic manufactured solution and invariants.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import nopcs_synth as S
+import oracle
+
+
+def test_scales_reproduce_printed_numbers():
+    """Re, M and the two sound speeds follow from the printed scales (Sec. 2, Sec. 4)."""
+    Us = math.sqrt(S.G_SI * S.L_SI)
+    assert abs(Us - 1.2131) < 1e-4            # sqrt(gL); the text's 12.131 is a typo
+    Re = 1.2256 * Us * S.L_SI / S.MU_S_SI
+    assert abs(Re - S.RE) / S.RE < 1e-4
+    a_hot = 1.0 / S.MACH * 1.2131             # a*/U_s = sqrt(T)/M, T = 1 (300 K)
+    a_cold = math.sqrt(100.0 / 300.0) / S.MACH * 1.2131
+    assert abs(a_hot - 347.21) < 0.02 and abs(a_cold - 200.46) < 0.02
+    assert abs(S.DT_ND - 6.2189e-7) < 1e-10
+
+
+def test_mach_diagnostic_uses_sqrt_T_over_M():
+    p = S.box_params((9, 9, 9), perturb_amp=0.0, T_lower=1.0)
+    s = oracle.Solver(p)
+    Q = s.initial_state()
+    # impose a uniform velocity of 10 cm/s in physical units at T = 1
+    V = 0.1 / 1.2131
+    Q[1] = Q[0] * V
+    Q[4] += 0.5 * Q[0] * V * V
+    d = s.diagnostics(Q)
+    assert abs(d["max_mach"] - 0.1 / 347.21) / (0.1 / 347.21) < 1e-4
+
+
+def test_hydrostatic_profile_integral_form():
+    """p(z1) - p(z2) = integral of rho g dz over [z1, z2] (trapezoid on a fine grid)."""
+    p = S.box_params((5, 5, 20001), length=(1.0, 1.0, 1.0), T_lower=5 / 3, T_upper=1.0)
+    rho, pr = oracle.base_profile(p)
+    z = np.linspace(0.0, 1.0, 20001)
+    lo = z < 0.5
+    for sel in (lo, ~lo):
+        zz, rr, pp = z[sel], rho[sel], pr[sel]
+        integral = np.trapezoid(rr, zz)
+        assert abs((pp[0] - pp[-1]) - integral) < 1e-7 * integral
+    # equation of state on each side and pressure continuity at the interface
+    gm2 = S.GAMMA * S.MACH ** 2
+    assert np.allclose(rho[lo] * (5 / 3), gm2 * pr[lo], rtol=1e-14)
+    assert np.allclose(rho[~lo] * 1.0, gm2 * pr[~lo], rtol=1e-14)
+    assert abs(pr[10000] - 1 / gm2) / (1 / gm2) < 1e-5
+
+
+def test_initial_state():
+    p = S.box_params((12, 10, 14), seed=3)
+    s = oracle.Solver(p)
+    Q = s.initial_state()
+    m = Q[1:4] / Q[0]
+    assert np.max(np.abs(m)) <= 1e-6
+    assert np.max(np.abs(m)) > 5e-7
+    for c in range(3):
+        for sl in (np.s_[:, :, 0], np.s_[:, :, -1], np.s_[:, 0, :], np.s_[:, -1, :], np.s_[0], np.s_[-1]):
+            assert np.all(Q[1 + c][sl] == 0.0)
+    # upper half (z >= 1/2) is the cold, dense fluid
+    assert Q[0][-2].mean() > Q[0][1].mean() * 1.5
+
+
+def test_diagnostics_closed_form():
+    p = S.box_params((6, 7, 8), perturb_amp=0.0, g=0.0, T_lower=1.0)
+    s = oracle.Solver(p)
+    Q = s.initial_state()
+    Q[0] = 2.0
+    Q[4] = 3.0
+    d = s.diagnostics(Q)
+    h = 1.0 / 5
+    assert abs(d["mass"] - 2.0 * 6 * 7 * 8 * h ** 3) < 1e-12
+    assert abs(d["energy_total"] - 3.0 * 6 * 7 * 8 * h ** 3) < 1e-12
+    assert d["nonfinite"] == 0
+    Q[4, 1, 2, 3] = np.nan
+    assert s.diagnostics(Q)["nonfinite"] == 1
+
+
+# --------------------------------------------------------------- manufactured RHS
+
+def _manufactured(params):
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z")
+    pi = sp.pi
+    rho = 1 + sp.Rational(1, 5) * sp.sin(2 * pi * x + 0.3) * sp.cos(pi * y) + sp.Rational(1, 10) * sp.cos(2 * pi * z + 0.2)
+    u = sp.Rational(3, 10) * sp.sin(pi * x + 0.2) * sp.cos(2 * pi * y + 0.5) * sp.sin(pi * z + 0.1)
+    v = sp.Rational(1, 4) * sp.cos(pi * x + 0.7) * sp.sin(pi * y + 0.4) * sp.cos(2 * pi * z)
+    w = sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(pi * y + 0.3) * sp.sin(pi * z + 0.6)
+    T = 1 + sp.Rational(1, 5) * sp.cos(pi * x + 0.4) * sp.sin(pi * y + 0.7) * sp.cos(pi * z)
+    g_, M, Re, Pr, gam = (params[k] for k in ("g", "M", "Re", "Pr", "gamma"))
+    Sut = params["suth_S"]
+    p = rho * T / (gam * M ** 2)
+    E = p / (gam - 1) + rho * (u ** 2 + v ** 2 + w ** 2) / 2
+    mu = T ** sp.Rational(3, 2) * (1 + Sut) / (T + Sut)
+    mub = params["mub_scale"] * 1e-4 * (3.381 * T * params["Ts_kelvin"] - 7.383) / params["mu_s_si"]
+    X = (x, y, z)
+    V = (u, v, w)
+    div = sum(sp.diff(V[a], X[a]) for a in range(3))
+    tau = [[None] * 3 for _ in range(3)]
+    for a in range(3):
+        for b in range(3):
+            if a == b:
+                tau[a][b] = ((sp.Rational(4, 3) * mu + mub) * sp.diff(V[a], X[a])
+                             + (-sp.Rational(2, 3) * mu + mub) * (div - sp.diff(V[a], X[a]))) / Re
+            else:
+                tau[a][b] = mu / Re * (sp.diff(V[a], X[b]) + sp.diff(V[b], X[a]))
+    kq = 1 / ((gam - 1) * Pr * Re * M ** 2)
+    q = [-mu * kq * sp.diff(T, X[a]) for a in range(3)]
+    Q = [rho, rho * u, rho * v, rho * w, E]
+    R = [0] * 5
+    for d in range(3):
+        ud = V[d]
+        conv = [rho * ud, rho * ud * u, rho * ud * v, rho * ud * w, (E + p) * ud]
+        conv[1 + d] += p
+        visc = [0, tau[d][0], tau[d][1], tau[d][2], u * tau[d][0] + v * tau[d][1] + w * tau[d][2] - q[d]]
+        for c in range(5):
+            R[c] += -sp.diff(conv[c], X[d]) + sp.diff(visc[c], X[d])
+    ga = params["gravity_axis"]
+    R[1 + ga] += -rho * g_
+    R[4] += -rho * V[ga] * g_
+    fQ = [sp.lambdify((x, y, z), e, "numpy") for e in Q]
+    fR = [sp.lambdify((x, y, z), e, "numpy") for e in R]
+    return fQ, fR
+
+
+def _mms_errors(params, Ns):
+    fQ, fR = _manufactured(params)
+    errs = []
+    for N in Ns:
+        p = dict(params)
+        p["n"] = (N, N, N)
+        p["len"] = (1.0, 1.0, 1.0)
+        p["sub_n"] = (N // 2, 7, 0)
+        s = oracle.Solver(p)
+        zz, yy, xx = np.meshgrid(*(np.linspace(0, 1, N),) * 3, indexing="ij")
+        Q = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fQ]).astype(np.float64)
+        Rex = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fR])
+        R = s.rhs(Q)
+        inner = np.s_[:, 2:-2, 2:-2, 2:-2]
+        e = np.abs(R - Rex)[inner].reshape(5, -1).max(axis=1) / np.abs(Rex[inner]).reshape(5, -1).max(axis=1)
+        errs.append(e)
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("base_subtract", [0, 1])
+def test_manufactured_rhs_converges(base_subtract):
+    """The discrete RHS converges at second order to the symbolic RHS of
+    Eqs. ge17-ge20 and bv1-bv3 (parameters chosen so that every term matters)."""
+    # isothermal base: the two-temperature base pressure has a kink whose
+    # compact derivative does not converge in the max norm at the interface
+    params = S.box_params((5, 5, 5), Re=10.0, M=0.5, mub_scale=1e-3, base_subtract=base_subtract,
+                          perturb_amp=0.0, T_lower=1.0)
+    errs = _mms_errors(params, (17, 33, 65))
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(errs[-1] < 5e-3), errs
+    assert np.all(rates[-1] > 1.7), (errs, rates)
+
+
+def test_manufactured_rhs_detects_planted_bulk_viscosity_error():
+    """With mu_b removed from the oracle's parameters the discrete RHS no longer
+    matches the symbolic RHS that includes it: the pin sees that term."""
+    params = S.box_params((5, 5, 5), Re=10.0, M=0.5, mub_scale=1e-3, perturb_amp=0.0)
+    fQ, fR = _manufactured(params)
+    planted = dict(params, mub_scale=0.0)
+    N = 33
+    p = dict(planted, n=(N, N, N), len=(1.0, 1.0, 1.0), sub_n=(0, 0, 0))
+    zz, yy, xx = np.meshgrid(*(np.linspace(0, 1, N),) * 3, indexing="ij")
+    Q = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fQ]).astype(np.float64)
+    Rex = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fR])
+    R = oracle.Solver(p).rhs(Q)
+    inner = np.s_[1, 2:-2, 2:-2, 2:-2]
+    e = np.abs(R - Rex)[inner].max() / np.abs(Rex[inner]).max()
+    good = _mms_errors(params, (33,))[0][1]
+    assert e > 10 * good
+
+
+def test_manufactured_rhs_paper_parameters():
+    params = S.box_params((5, 5, 5), perturb_amp=0.0, base_subtract=1, T_lower=1.0)
+    errs = _mms_errors(params, (17, 33))
+    assert np.all(errs[1] < errs[0]), errs
+
+
+# --------------------------------------------------------------- invariants
+
+def test_isothermal_rest_state():
+    """Isothermal quiescent box with gravity stays at rest (to round-off)."""
+    for bs in (0, 1):
+        p = S.box_params((12, 12, 16), sub_n=(5, 5, 5), T_upper=1.0, T_lower=1.0, perturb_amp=0.0,
+                         base_subtract=bs)
+        s = oracle.Solver(p)
+        Q0 = s.initial_state()
+        Q = s.step(Q0, 3)
+        assert np.max(np.abs(Q[1:4])) < 1e-12
+        assert np.max(np.abs(Q[0] - Q0[0])) < 1e-13
+        assert np.max(np.abs(Q[4] - Q0[4]) / Q0[4]) < 1e-14
+
+
+def test_uniform_state_without_gravity_is_steady():
+    p = S.box_params((9, 10, 11), sub_n=(4, 4, 4), T_upper=1.0, T_lower=1.0, perturb_amp=0.0, g=0.0)
+    s = oracle.Solver(p)
+    Q0 = s.initial_state()
+    R = s.rhs(Q0)
+    assert np.max(np.abs(R[0])) < 1e-12 and np.max(np.abs(R[1:4])) < 1e-9
+    assert np.max(np.abs(R[4])) < 1e-8
+
+
+@pytest.mark.parametrize("bs", [0, 1])
+def test_mirror_symmetry_of_unperturbed_box(bs):
+    """Square cross-section, no perturbation: x -> L-x, y -> L-y and x <-> y
+    symmetries are kept by the discrete solver."""
+    p = S.box_params((14, 14, 16), sub_n=(6, 6, 6), perturb_amp=0.0, base_subtract=bs, dt=2e-5)
+    s = oracle.Solver(p)
+    Q = s.step(s.initial_state(), 4)
+    rho, mu, mv, mw, E = Q
+    scale = [np.max(np.abs(f)) for f in Q]
+    assert scale[1] > 0 and scale[3] > 0
+    # plain form: the momentum equation differentiates p ~ 1/(gamma M^2) = 5.9e4,
+    # whose round-off (eps p dt / h per stage) bounds the achievable symmetry
+    floor = 0.0 if bs else 1e-13
+
+    def close(a, b, c):
+        return np.max(np.abs(a - b)) <= max(1e-12 * scale[c], floor if c in (1, 2, 3) else 0.0)
+
+    flipx = lambda f: f[:, :, ::-1]
+    flipy = lambda f: f[:, ::-1, :]
+    swap = lambda f: np.swapaxes(f, 1, 2)
+    assert close(rho, flipx(rho), 0) and close(E, flipx(E), 4)
+    assert close(mu, -flipx(mu), 1) and close(mv, flipx(mv), 2) and close(mw, flipx(mw), 3)
+    assert close(rho, flipy(rho), 0) and close(mv, -flipy(mv), 2) and close(mu, flipy(mu), 1)
+    assert close(rho, swap(rho), 0) and close(mu, swap(mv), 1) and close(mw, swap(mw), 3)
+
+
+def test_conservation_closed_box():
+    """Closed adiabatic box: mass and total energy drift only at truncation level."""
+    p = S.box_params((24, 24, 24), sub_n=(12, 12, 12), filter_every=0)
+    s = oracle.Solver(p)
+    Q0 = s.initial_state()
+    d0 = s.diagnostics(Q0)
+    Q = s.step(Q0, 20)
+    d1 = s.diagnostics(Q)
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-10
+    assert abs(d1["energy_total"] - d0["energy_total"]) / d0["energy_total"] < 1e-10
+
+
+def test_rk4_temporal_order():
+    """Classical RK4: halving dt divides the error at a fixed time by ~16."""
+    base = S.box_params((10, 10, 10), sub_n=(5, 5, 5), Re=100.0, M=0.5, mub_scale=1e-3,
+                        perturb_amp=3e-2, filter_every=0, T_lower=1.2)
+    T_end = 0.08
+    out = {}
+    for nst in (4, 8, 64):
+        p = dict(base, dt=T_end / nst)
+        s = oracle.Solver(p)
+        out[nst] = s.step(s.initial_state(), nst)
+    e1 = np.max(np.abs(out[4] - out[64])[1:4])
+    e2 = np.max(np.abs(out[8] - out[64])[1:4])
+    assert 12.0 < e1 / e2 < 20.0, e1 / e2
+
+
+def test_wall_bc_properties():
+    p = S.box_params((8, 9, 10), perturb_amp=1e-3)
+    s = oracle.Solver(p)
+    rng = np.random.default_rng(2)
+    Q = s.initial_state()
+    Q[1:4] = rng.uniform(-1e-3, 1e-3, Q[1:4].shape)
+    Q[4] *= 1 + 1e-3 * rng.standard_normal(Q[4].shape)
+    Qb = s.wall_bc(Q)
+    gam, M = p["gamma"], p["M"]
+    T = gam * M ** 2 * (gam - 1) * (Qb[4] - 0.5 * (Qb[1] ** 2 + Qb[2] ** 2 + Qb[3] ** 2) / Qb[0]) / Qb[0]
+    for c in (1, 2, 3):
+        assert np.all(Qb[c][:, :, 0] == 0) and np.all(Qb[c][0] == 0) and np.all(Qb[c][:, -1, :] == 0)
+    # face node on x = 0: zero one-sided normal gradient of T
+    g = -3 * T[4, 4, 0] + 4 * T[4, 4, 1] - T[4, 4, 2]
+    assert abs(g) < 1e-12
+    # edge node (x = 0, y = 0): mean of the two one-sided extrapolations
+    ex = (4 * T[4, 0, 1] - T[4, 0, 2]) / 3
+    ey = (4 * T[4, 1, 0] - T[4, 2, 0]) / 3
+    assert abs(T[4, 0, 0] - 0.5 * (ex + ey)) < 1e-12
+    # interior untouched, density untouched
+    assert np.array_equal(Qb[:, 1:-1, 1:-1, 1:-1], Q[:, 1:-1, 1:-1, 1:-1])
+    assert np.array_equal(Qb[0], Q[0])

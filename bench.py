@@ -1,0 +1,324 @@
+"""Benchmark of the NOHAP/OUCS3 compressible Navier-Stokes RK step on GB300.
+
+Metric: RK-stage grid-point updates per second (points x 4 stages x steps /
+time) of the mixed-precision form at 1024^3 (FP32 fluxes/derivatives on the
+state minus its hydrostatic base, FP64 state and RK accumulation, NOHAP
+sub-domains of 64), one RK4 step per benchmark step, the filter on its
+every-50-steps cadence, state resident in HBM.  Also reported: the plain FP64
+form, the dominant kernel against the HBM roofline, an end-to-end number
+through the C ABI with host buffers, and the FP64 CPU oracle as a baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own independent box (the path
+needs no exchange between boxes): weak scaling, no data-path collective.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK-stage grid-point updates/s at 1024^3 (mixed vs FP64), % of HBM/tensor roofline"
+UNIT = "point-stage updates/s"
+
+# algorithmic bytes per grid point of one launch of each kernel kind
+# (mixed form; see the design notes for the derivation)
+ALG_BYTES_MIXED = {
+    "prep": 40 + 24,                   # read Q (5 f64), write W (6 f32)
+    "sweep_x": 24 + 20,                # read W, write R (5 f32)
+    "sweep_y": 24 + 40,                # read W, read+write R
+    "sweep_z": 24 + 40,
+    "visc_rk_update": (164 + 204 + 204 + 124) / 4.0,  # W, R, FP64 registers; stage average
+    "filter": 3 * 80,                  # three sweeps, each read+write Q
+}
+ALG_BYTES_FP64 = {
+    "prep": 40 + 48, "sweep_x": 48 + 40, "sweep_y": 48 + 80, "sweep_z": 48 + 80,
+    "visc_rk_update": (188 + 228 * 2 + 148) / 4.0, "filter": 3 * 80,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024, help="grid points per axis")
+    ap.add_argument("--sub-n", type=int, default=64)
+    ap.add_argument("--fp64-n", type=int, default=1024, help="grid of the FP64-form comparison (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-n", type=int, default=64, help="oracle sample grid for the CPU baseline")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": loaded[len(loaded) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def box(n, sub_n, **kw):
+    import nopcs_synth as S
+    return S.box_params((n, n, n), sub_n=(sub_n,) * 3, **kw)
+
+
+def run_cpu_oracle(n, steps, warmup=0):
+    """Time the FP64 oracle as it stands (OpenMP, all host cores)."""
+    import oracle
+    p = box(n, min(64, n))
+    p["base_subtract"] = 1
+    s = oracle.Solver(p)
+    Q = s.initial_state()
+    if warmup:
+        Q = s.step(Q, warmup)
+    t0 = time.perf_counter()
+    Q = s.step(Q, steps)
+    dt = time.perf_counter() - t0
+    pts = float(n) ** 3 * 4 * steps
+    return pts / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.cpu_n
+    rate, dt, cores = run_cpu_oracle(n, args.steps, args.warmup)
+    sample = "FP64 CPU oracle, %d^3 box of the same physics (base-subtracted), %d RK4 steps after %d warm-up" % (
+        n, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "two-temperature RTI box %d^3 (oracle sample of the 1024^3 workload)" % n},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2203_00879_gb300 import build as B
+    B.build()
+    from paper_2203_00879_gb300 import nopcs as N
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    st = stream.cuda_stream
+    n, K, W = args.n, args.steps, args.warmup
+    npts = float(n) ** 3
+    p = box(n, args.sub_n, seed=1 + rank)
+    ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=st)
+    N.nopcs_rk_step(ctx, W)
+    N.nopcs_synchronize(ctx)
+    N.nopcs_set_profiling(ctx, True)
+    N.nopcs_profile_read(ctx, reset=True)
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.start()
+    ev0.record(stream)
+    N.nopcs_rk_step(ctx, K)
+    diag = N.nopcs_diagnostics(ctx, 0)  # result read back (D2H) inside the timed region
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = N.nopcs_profile_read(ctx, reset=True)
+    N.nopcs_set_profiling(ctx, False)
+    ms_max = max_over_ranks(ms)
+    value = world * npts * 4 * K / (ms_max * 1e-3)
+    launches_per_kind = {"prep": 1, "sweep_x": 1, "sweep_y": 1, "sweep_z": 1, "visc_rk_update": 1,
+                         "wall_bc": 2, "filter": 3, "diagnostics": 2}
+    gpu_launches = int(sum(v[1] * launches_per_kind.get(k, 1) for k, v in prof.items()))
+
+    # dominant kernel against the HBM roofline
+    hbm, peak_kind = peaks()
+    dom = max((k for k in prof if k in ALG_BYTES_MIXED), key=lambda k: prof[k][0])
+    avg_ms = prof[dom][0] / max(prof[dom][1], 1)
+    alg = ALG_BYTES_MIXED[dom] * npts
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            tr = json.load(f)
+        from paper_2203_00879_gb300.build import source_hash
+        ent = tr.get("mixed", {}).get(dom)
+        if ent and ent.get("source_hash") == source_hash():
+            traffic = ent["bytes_per_point"] * npts
+    except Exception:
+        traffic = None
+    per_kernel = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(ms, 1e-9)} for k, v in prof.items()
+                  if v[1]}
+    N.nopcs_destroy(ctx)
+    torch.cuda.synchronize()
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # state from pinned host memory, advances one RK4 step and reads the
+    # diagnostics back
+    e2e = None
+    if args.e2e_steps > 0:
+        ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=st)
+        nbytes = int(5 * npts * 8)
+        try:
+            host = torch.empty(int(5 * npts), dtype=torch.float64, pin_memory=True)
+            pinned = True
+        except Exception:
+            host = torch.empty(int(5 * npts), dtype=torch.float64)
+            pinned = False
+        N.nopcs_get_state(ctx, 0, host.data_ptr())
+        N.nopcs_set_state(ctx, 0, host.data_ptr())
+        N.nopcs_rk_step(ctx, 1)
+        N.nopcs_diagnostics(ctx, 0)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            N.nopcs_set_state(ctx, 0, host.data_ptr())
+            N.nopcs_rk_step(ctx, 1)
+            N.nopcs_diagnostics(ctx, 0)
+        barrier()
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * npts * 4 * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": 10 * 8, "pinned_host": pinned, "steps": args.e2e_steps}
+        del host
+        N.nopcs_destroy(ctx)
+        torch.cuda.synchronize()
+
+    # plain FP64 form for comparison
+    fp64 = None
+    if args.fp64_n > 0:
+        n64 = args.fp64_n
+        p64 = box(n64, args.sub_n, seed=1 + rank)
+        try:
+            ctx = N.nopcs_init([p64], prec=N.NOPCS_FP64, stream=st)
+        except N.NopcsError:
+            n64 = 768
+            p64 = box(n64, args.sub_n, seed=1 + rank)
+            ctx = N.nopcs_init([p64], prec=N.NOPCS_FP64, stream=st)
+        N.nopcs_rk_step(ctx, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        N.nopcs_rk_step(ctx, args.fp64_steps)
+        e1.record(stream)
+        barrier()
+        m64 = max_over_ranks(e0.elapsed_time(e1))
+        v64 = world * float(n64) ** 3 * 4 * args.fp64_steps / (m64 * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "grid": [n64] * 3, "steps": args.fp64_steps,
+                "ms_per_step": m64 / args.fp64_steps, "mixed_over_fp64": value / v64}
+        N.nopcs_destroy(ctx)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, dt, cores = run_cpu_oracle(args.cpu_n, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 CPU oracle, one RK4 step of a %d^3 box of the same physics (base-subtracted), "
+                         "%.1f s" % (args.cpu_n, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "two-temperature Rayleigh-Taylor box %d^3, mixed precision (FP32 fluxes and "
+                                   "NOHAP derivatives, FP64 state and RK4), sub-domains of %d, filter every 50 "
+                                   "steps" % (n, args.sub_n),
+                       "grid": [n, n, n], "sub_n": args.sub_n, "precision": "mixed", "form": "thomas",
+                       "l2": "inputs larger than L2 (FP64 state %.1f GB)" % (40 * npts / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                         "alg_bytes_per_point": ALG_BYTES_MIXED[dom], "avg_launch_ms": avg_ms},
+            "kernels": per_kernel,
+            "gpu_launches": gpu_launches,
+            "e2e": e2e,
+            "fp64_form": fp64,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "diagnostics": {"step": diag["step"], "max_speed": diag["max_speed"], "max_dp": diag["max_dp"]},
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

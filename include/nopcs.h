@@ -1,0 +1,214 @@
+/*
+ * nopcs.h -- C ABI of the GB300 (sm_103a) NOHAP/OUCS3 compressible Navier-Stokes
+ * hot path.
+ *
+ * The method is that of Sundaram, Sengupta & Sengupta, "Ultrasound triggering of
+ * Rayleigh-Taylor instability: solution of compressible Navier-Stokes equation
+ * by a non-overlapping parallel compact scheme" (arXiv 2203.00879):
+ *   - OUCS3 compact first derivative [A]{f'} = [B]{f} (Sec. 3, Eq. CS:AfpBf and
+ *     the interior coefficients printed after it), solved per non-overlapping
+ *     sub-domain with the NOHAP closure: sub-domain end points from the
+ *     equivalent explicit scheme f'_i = sum_k C_ik f_{i+k}, C = A^-1 B
+ *     (Eqs. CS:fpCf, CS:fpCf_i), interior points by the Thomas algorithm;
+ *   - the nondimensional compressible Navier-Stokes right-hand side with bulk
+ *     viscosity (Sec. 2, Eqs. ge1-ge20, reg, bv1-bv3), gravity source (Eq. ge8a),
+ *     classical RK4 and the implicit filter with coefficient 0.135 every 50 steps
+ *     (Sec. 4, first paragraph).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a nopcs_status and never aborts or throws.  On an error
+ *     other than NOPCS_ECUDA the context stays usable; nopcs_last_error() gives a
+ *     message.  Arguments are validated before any device work.
+ *   - Fields are SoA, x fastest: element (i, j, k) of an nx x ny x nz box is at
+ *     i + nx * (j + ny * k).  A state is 5 such fields in the order
+ *     rho, rho u, rho v, rho w, E (total energy per unit volume), nondimensional.
+ *   - Caller-owned buffers passed to an entry point are only read or written
+ *     during the work that call enqueues; the library keeps no pointer to them.
+ *     The library owns the state registers, scratch, operator tables and CUDA
+ *     graphs of a context and frees them in nopcs_destroy().
+ *   - Streams are cudaStream_t values passed as void* (NULL = legacy default).
+ *   - The library runs on the CUDA device current at nopcs_init().
+ */
+#ifndef NOPCS_H
+#define NOPCS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nopcs_ctx nopcs_ctx; /* opaque, library-owned */
+
+typedef enum {
+    NOPCS_OK = 0,
+    NOPCS_EINVAL = 1,      /* bad argument; nothing was enqueued                */
+    NOPCS_ENOMEM = 2,      /* device or host allocation failed                  */
+    NOPCS_ECUDA = 3,       /* a CUDA call failed; the context should be destroyed */
+    NOPCS_EUNSTABLE = 4,   /* non-finite values found in the state              */
+    NOPCS_ETIMEOUT = 5,    /* a bounded device wait gave up                     */
+    NOPCS_EUNSUPPORTED = 6 /* valid request this build does not implement       */
+} nopcs_status;
+
+typedef enum {
+    NOPCS_FP64 = 0, /* fluxes, derivatives, viscous terms and state in FP64      */
+    NOPCS_MIXED = 1 /* FP32 fluxes/derivatives/viscous terms on the state minus its
+                       hydrostatic base; FP64 state and RK accumulation          */
+} nopcs_precision;
+
+typedef enum {
+    NOPCS_FORM_AUTO = 0,   /* library picks the solve form per box              */
+    NOPCS_FORM_THOMAS = 1, /* per-sub-domain Thomas sweeps                      */
+    NOPCS_FORM_GEMM_3XTF32 = 2,
+    NOPCS_FORM_GEMM_BF16X3 = 3
+} nopcs_form;
+
+/*
+ * One box of the two-temperature Rayleigh-Taylor problem (Sec. 2, Fig. 1).
+ * Caller-owned; copied by nopcs_init.  Nondimensionalisation of Eqs. ge14/ge15:
+ * lengths by L, velocity by U_s = sqrt(gL), time by L/U_s, density by rho_s,
+ * pressure and energy by rho_s U_s^2 (so p = rho T / (gamma M^2)), temperature
+ * by T_s.
+ */
+typedef struct {
+    int n[3];              /* grid points per axis, >= 5; nodes lie on the walls    */
+    double len[3];         /* box lengths; spacing h = len / (n - 1)                */
+    int gravity_axis;      /* 0, 1 or 2: gravity points along -axis; the interface  */
+                           /* is the mid-plane normal to it                          */
+    int sub_n[3];          /* NOHAP sub-domain length per axis (>= 3); 0 or >= n:   */
+                           /* one sub-domain                                         */
+    double Re, M, Pr, gamma;
+    double suth_S;         /* Sutherland constant / T_s                             */
+    double mub_scale;      /* factor on the bulk-viscosity law, Eq. reg             */
+    double mu_s_si;        /* dimensional viscosity at T_s, Pa s (mu_b / mu_s)      */
+    double Ts_kelvin;      /* T_s in kelvin (Eq. reg takes T* in kelvin)            */
+    double T_upper, T_lower; /* nondimensional temperatures of the two halves       */
+    double g;              /* nondimensional gravity g L / U_s^2 (1)                 */
+    double dt;             /* nondimensional time step                              */
+    int filter_every;      /* filter after every this many steps; 0 = never         */
+    double filter_alpha;   /* filter coefficient (0.135)                            */
+    int base_subtract;     /* 1: differentiate p - p_h, source -(rho - rho_h) g.    */
+                           /* Forced to 1 under NOPCS_MIXED.                         */
+    unsigned long long seed; /* seed of the initial velocity perturbation           */
+    double perturb_amp;    /* amplitude of the uniform velocity perturbation        */
+} nopcs_box_desc;
+
+typedef struct {
+    double mass;           /* sum of rho times h_x h_y h_z                          */
+    double momentum[3];
+    double energy_total;   /* sum of E + rho g z, times the cell volume             */
+    double max_speed;      /* max |V|                                               */
+    double max_dp;         /* max |p - p_h| (disturbance pressure, Sec. 4)          */
+    double max_mach;       /* max |V| M / sqrt(T)                                   */
+    long long step;        /* RK steps taken by this box                            */
+    int nonfinite;         /* 1 if any state value is NaN or Inf                    */
+} nopcs_diag;
+
+/*
+ * Create a context for `nboxes` independent boxes, build the operator tables
+ * (Sec. 3: global C rows for sub-domain ends, Thomas factors), allocate the
+ * three FP64 RK registers plus scratch per box on the current device, and set
+ * every box to its initial state (quiescent hydrostatic two-temperature box
+ * with a SplitMix64 velocity perturbation on interior nodes).
+ * `stream` (cudaStream_t or NULL) is the stream of all later state work.
+ * Errors: EINVAL (n < 5, nboxes < 1, bad enum, sub_n in 1..2, ...), ENOMEM,
+ * ECUDA.  On error *out is NULL.
+ */
+nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision prec,
+                        nopcs_form form, void *stream, nopcs_ctx **out);
+
+/* Free everything the context owns (waits for its stream).  NULL is a no-op. */
+void nopcs_destroy(nopcs_ctx *ctx);
+
+/* Message of the last failed call on this context (or of the last failed
+ * nopcs_init when ctx is NULL); never NULL. */
+const char *nopcs_last_error(const nopcs_ctx *ctx);
+
+/*
+ * Copy a state (5 FP64 fields, np = nx*ny*nz each) into / out of box `box`.
+ * `q` may be host (pageable or pinned) or device memory; the copy is enqueued
+ * on the context stream and the call returns after it completes.
+ */
+nopcs_status nopcs_set_state(nopcs_ctx *ctx, int box, const double *q);
+nopcs_status nopcs_get_state(nopcs_ctx *ctx, int box, double *q);
+
+/* Reset box `box` to its initial state and its step counter to 0. */
+nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box);
+
+/*
+ * NOHAP compact derivative of one field of box `box`'s shape along `axis`
+ * (0 = x, 1 = y, 2 = z), scaled by 1/h_axis.  order 1: the OUCS3 first
+ * derivative (Sec. 3).  order 2: the first-derivative operator applied twice
+ * (the paper prints no compact second derivative; this reading is stated in the
+ * design notes).  dtype 0: f and df are FP64 and the arithmetic is FP64 with C
+ * rows truncated at |C| < 1e-16 (48 taps each side, Sec. 3); dtype 1: FP32 with
+ * C rows truncated at |C| < 1e-8 (24 taps each side).  f and df are device
+ * pointers of np elements, must not overlap; the work is enqueued on `stream`
+ * and the call does not wait.  order 2 uses library-owned scratch of np
+ * elements.  Errors: EINVAL, ECUDA.
+ */
+nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int dtype,
+                              const void *f, void *df, void *stream);
+
+/*
+ * Advance every box by `nsteps` classical RK4 steps of dt (Sec. 4), applying
+ * the no-slip adiabatic wall conditions after every stage and the filter after
+ * every filter_every steps (counted per box from its initial state).  Enqueued
+ * on the context stream; the call returns without waiting.  Errors: EINVAL
+ * (nsteps < 0), ECUDA.
+ */
+nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps);
+
+/*
+ * Evaluate the right-hand side of Eq. ge17 for the FP64 state `q` (device, 5
+ * fields) of box `box` into `r` (device, 5 fields, FP64 under NOPCS_FP64 and
+ * FP32 under NOPCS_MIXED), with exactly the arithmetic one RK stage uses.  The
+ * momentum right-hand side is zero on wall nodes (no-slip).  Waits for
+ * completion.  Does not change the box state.
+ */
+nopcs_status nopcs_rhs(nopcs_ctx *ctx, int box, const double *q, void *r);
+
+/* Apply the filter (Sec. 4) to box `box`'s state now.  Enqueued; no wait. */
+nopcs_status nopcs_filter(nopcs_ctx *ctx, int box);
+
+/*
+ * Reduce box `box`'s state to the diagnostics above (FP64 accumulation in a
+ * fixed order, so repeated calls on the same state give identical bits).
+ * Waits for the context stream.  Returns NOPCS_EUNSTABLE (with *out filled) if
+ * the state holds a non-finite value.
+ */
+nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out);
+
+/* Wait for all work enqueued on the context stream. */
+nopcs_status nopcs_synchronize(nopcs_ctx *ctx);
+
+/*
+ * Per-kernel timing.  With profiling on, nopcs_rk_step launches its kernels
+ * directly (no CUDA graph) between pairs of CUDA events on the context stream;
+ * nopcs_profile_read waits for the stream and returns, per kernel kind, the
+ * summed event time in milliseconds and the launch count since the last reset
+ * (arrays of NOPCS_NUM_KERNELS entries).  nopcs_kernel_name gives the kind's
+ * name (static string; NULL for an out-of-range id).
+ */
+#define NOPCS_NUM_KERNELS 8
+nopcs_status nopcs_set_profiling(nopcs_ctx *ctx, int on);
+nopcs_status nopcs_profile_read(nopcs_ctx *ctx, double *ms, long long *launches, int reset);
+const char *nopcs_kernel_name(int kind);
+
+/*
+ * Host-side operator tables, for inspection and tests; needs no GPU.
+ * For a line of N points split into sub-domains of sub_n (kind 0: OUCS3 first
+ * derivative, dimensionless, i.e. times h; kind 1: filter with coefficient
+ * `alpha_f`), C rows truncated at |C| < thresh:
+ *   starts[0..nsub]      sub-domain starts and N (caller array of N+1 ints),
+ *   end_j0[2*nsub], end_len[2*nsub]  first column and tap count of the end row
+ *                        of each sub-domain (start, then end),
+ *   coef[]               the concatenated taps (capacity max_coef doubles).
+ * Returns EINVAL on bad sizes or too small buffers; *nsub is set on success.
+ */
+nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double alpha_f, double thresh,
+                                 int *nsub, int *starts, int *end_j0, int *end_len,
+                                 double *coef, int max_coef);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NOPCS_H */

@@ -1,0 +1,629 @@
+// C ABI of libnopcs (declared in include/nopcs.h): context, state registers,
+// the RK4 stage sequence and its CUDA-graph replay, per-kernel event timing.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "nopcs_internal.cuh"
+
+using namespace nopcs;
+
+namespace {
+
+const char *const KERNEL_NAMES[NOPCS_NUM_KERNELS] = {"prep",         "sweep_x", "sweep_y", "sweep_z",
+                                                     "visc_rk_update", "wall_bc", "filter",  "diagnostics"};
+enum { K_PREP = 0, K_SX, K_SY, K_SZ, K_VISC, K_BC, K_FILTER, K_DIAG };
+
+thread_local std::string g_init_error;
+
+struct BoxRes {
+    nopcs_box_desc d{};
+    BoxDev dev{};
+    LineOpBuf dop64[3], dop32[3], fop[3];
+    double *Q = nullptr;  // 3 registers of 5 fields: Qn, Qs, acc
+    void *W = nullptr, *R = nullptr;
+    void *base = nullptr;
+    double *partial = nullptr, *diag_out = nullptr;
+    void *scratch = nullptr;  // order-2 derivative intermediate (lazy)
+    int nblk_diag = 0;
+    long long step = 0;
+    double *Qn() const { return Q; }
+    double *Qs() const { return Q + 5 * dev.np; }
+    double *acc() const { return Q + 10 * dev.np; }
+};
+
+struct ProfPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+}  // namespace
+
+struct nopcs_ctx {
+    int device = 0;
+    nopcs_precision prec = NOPCS_FP64;
+    nopcs_form form = NOPCS_FORM_THOMAS;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<BoxRes> boxes;
+    std::string err;
+    cudaGraphExec_t step_exec = nullptr;
+    bool profiling = false;
+    std::vector<ProfPair> pool;
+    size_t pool_used = 0;
+    double prof_ms[NOPCS_NUM_KERNELS] = {};
+    long long prof_n[NOPCS_NUM_KERNELS] = {};
+};
+
+namespace {
+
+nopcs_status fail(nopcs_ctx *c, nopcs_status s, const std::string &m)
+{
+    if (c)
+        c->err = m;
+    else
+        g_init_error = m;
+    return s;
+}
+
+nopcs_status cuda_fail(nopcs_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, NOPCS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+bool valid_box(const nopcs_box_desc &d, std::string &m)
+{
+    for (int a = 0; a < 3; ++a) {
+        if (d.n[a] < 5) {
+            m = "each axis needs at least 5 points";
+            return false;
+        }
+        if (!(d.len[a] > 0.0)) {
+            m = "box lengths must be positive";
+            return false;
+        }
+        if (d.sub_n[a] < 0 || (d.sub_n[a] > 0 && d.sub_n[a] < 3)) {
+            m = "sub_n must be 0 or >= 3";
+            return false;
+        }
+    }
+    if (d.gravity_axis < 0 || d.gravity_axis > 2) {
+        m = "gravity_axis must be 0, 1 or 2";
+        return false;
+    }
+    if (!(d.Re > 0 && d.M > 0 && d.Pr > 0 && d.gamma > 1.0 && d.dt > 0 && d.Ts_kelvin > 0 && d.mu_s_si > 0 &&
+          d.T_upper > 0 && d.T_lower > 0 && d.suth_S >= 0)) {
+        m = "physical parameters out of range";
+        return false;
+    }
+    if (d.filter_every < 0 || !(d.filter_alpha > -0.5 && d.filter_alpha < 0.5)) {
+        m = "filter_every must be >= 0 and |filter_alpha| < 0.5";
+        return false;
+    }
+    return true;
+}
+
+// Hydrostatic base (Sec. 2): dp/dz = -rho g, rho = gamma M^2 p / T, constant T
+// in each half, p = 1 / (gamma M^2) at the mid-plane.
+void hydrostatic(const nopcs_box_desc &d, std::vector<double> &rho, std::vector<double> &p)
+{
+    const int ga = d.gravity_axis, N = d.n[ga];
+    const double h = d.len[ga] / (N - 1), zI = 0.5 * d.len[ga];
+    const double gm2 = d.gamma * d.M * d.M;
+    rho.resize(N);
+    p.resize(N);
+    for (int k = 0; k < N; ++k) {
+        const double z = k * h;
+        const double T = z < zI ? d.T_lower : d.T_upper;
+        p[k] = exp(-gm2 * d.g * (z - zI) / T) / gm2;
+        rho[k] = gm2 * p[k] / T;
+    }
+}
+
+size_t esize(const nopcs_ctx *c) { return c->prec == NOPCS_MIXED ? 4 : 8; }
+
+void free_box(BoxRes &b)
+{
+    for (int a = 0; a < 3; ++a) {
+        b.dop64[a].release();
+        b.dop32[a].release();
+        b.fop[a].release();
+    }
+    if (b.Q) cudaFree(b.Q);
+    if (b.W) cudaFree(b.W);
+    if (b.R) cudaFree(b.R);
+    if (b.base) cudaFree(b.base);
+    if (b.partial) cudaFree(b.partial);
+    if (b.scratch) cudaFree(b.scratch);
+    b.Q = nullptr;
+    b.W = b.R = b.base = b.scratch = nullptr;
+    b.partial = b.diag_out = nullptr;
+}
+
+nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
+{
+    const nopcs_box_desc &d = b.d;
+    BoxDev &x = b.dev;
+    for (int a = 0; a < 3; ++a) {
+        x.n[a] = d.n[a];
+        x.h[a] = d.len[a] / (d.n[a] - 1);
+        x.inv_h[a] = 1.0 / x.h[a];
+    }
+    x.np = (long long)d.n[0] * d.n[1] * d.n[2];
+    x.ga = d.gravity_axis;
+    x.gamma = d.gamma;
+    x.gm2 = d.gamma * d.M * d.M;
+    x.Re = d.Re;
+    x.M = d.M;
+    x.kq = 1.0 / ((d.gamma - 1.0) * d.Pr * d.Re * d.M * d.M);
+    x.suth_S = d.suth_S;
+    // Eq. reg over mu_s: mu_b / mu_s = mub_scale 1e-4 (3.381 T T_s - 7.383) / mu_s
+    x.mub_coef0 = d.mub_scale * 1.0e-4 * 3.381 * d.Ts_kelvin / d.mu_s_si;
+    x.mub_coef1 = -d.mub_scale * 1.0e-4 * 7.383 / d.mu_s_si;
+    x.g = d.g;
+    x.cE = 1.0 / (d.gamma * (d.gamma - 1.0) * d.M * d.M);
+    x.dt = d.dt;
+
+    std::string msg;
+    for (int a = 0; a < 3; ++a) {
+        if (!build_line_op(d.n[a], d.sub_n[a], KIND_DERIV, 0.0, 1e-16, b.dop64[a].host, msg) ||
+            !build_line_op(d.n[a], d.sub_n[a], KIND_DERIV, 0.0, 1e-8, b.dop32[a].host, msg) ||
+            !build_line_op(d.n[a], d.sub_n[a], KIND_FILTER, d.filter_alpha, 1e-16, b.fop[a].host, msg))
+            return fail(ctx, NOPCS_EINVAL, msg);
+        CK(b.dop64[a].upload(), "operator upload");
+        CK(b.dop32[a].upload(), "operator upload");
+        CK(b.fop[a].upload(), "operator upload");
+    }
+    // base tables
+    std::vector<double> rh, ph;
+    hydrostatic(d, rh, ph);
+    const int Ng = d.n[d.gravity_axis];
+    const bool bs = d.base_subtract != 0;
+    // layout: rho_h, p_h, rho_b, p_b, E_b, H_b (double) then rho_b, p_b, H_b (float)
+    std::vector<double> t64(6 * (size_t)Ng, 0.0);
+    std::vector<float> t32(3 * (size_t)Ng, 0.0f);
+    for (int k = 0; k < Ng; ++k) {
+        t64[k] = rh[k];
+        t64[Ng + k] = ph[k];
+        if (bs) {
+            const double Eb = ph[k] / (d.gamma - 1.0);
+            t64[2 * Ng + k] = rh[k];
+            t64[3 * Ng + k] = ph[k];
+            t64[4 * Ng + k] = Eb;
+            t64[5 * Ng + k] = Eb + ph[k];
+            t32[k] = (float)rh[k];
+            t32[Ng + k] = (float)ph[k];
+            t32[2 * Ng + k] = (float)(Eb + ph[k]);
+        }
+    }
+    const size_t b64 = t64.size() * 8, b32 = t32.size() * 4;
+    CK(cudaMalloc(&b.base, b64 + b32 + 256), "base tables");
+    CK(cudaMemcpy(b.base, t64.data(), b64, cudaMemcpyHostToDevice), "base tables");
+    CK(cudaMemcpy((char *)b.base + b64, t32.data(), b32, cudaMemcpyHostToDevice), "base tables");
+    const double *p64 = (const double *)b.base;
+    const float *p32 = (const float *)((const char *)b.base + b64);
+    x.rho_h64 = p64;
+    x.p_h64 = p64 + Ng;
+    x.rho_b64 = p64 + 2 * Ng;
+    x.p_b64 = p64 + 3 * Ng;
+    x.E_b64 = p64 + 4 * Ng;
+    x.H_b64 = p64 + 5 * Ng;
+    x.rho_b32 = p32;
+    x.p_b32 = p32 + Ng;
+    x.H_b32 = p32 + 2 * Ng;
+
+    // state registers and scratch
+    const size_t np = (size_t)x.np;
+    cudaError_t e = cudaMalloc(&b.Q, 15 * np * sizeof(double));
+    if (e != cudaSuccess) {
+        b.Q = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "state registers");
+    }
+    e = cudaMalloc(&b.W, 6 * np * esize(ctx));
+    if (e != cudaSuccess) {
+        b.W = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "primitive buffer");
+    }
+    e = cudaMalloc(&b.R, 5 * np * esize(ctx));
+    if (e != cudaSuccess) {
+        b.R = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "right-hand-side buffer");
+    }
+    b.nblk_diag = diag_blocks(x.np);
+    CK(cudaMalloc(&b.partial, ((size_t)b.nblk_diag * 10 + 16) * sizeof(double)), "diagnostics scratch");
+    b.diag_out = b.partial + (size_t)b.nblk_diag * 10;
+    CK(launch_initial_state(x, d.seed, d.perturb_amp, b.Qn(), ctx->stream), "initial state");
+    b.step = 0;
+    return NOPCS_OK;
+}
+
+// ---- profiling --------------------------------------------------------------
+void harvest(nopcs_ctx *c)
+{
+    for (size_t i = 0; i < c->pool_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->pool[i].a, c->pool[i].b) == cudaSuccess) {
+            c->prof_ms[c->pool[i].kind] += ms;
+            c->prof_n[c->pool[i].kind] += 1;
+        }
+    }
+    c->pool_used = 0;
+}
+
+struct Timed {
+    nopcs_ctx *c;
+    cudaStream_t st;
+    int kind;
+    ProfPair *pp = nullptr;
+    Timed(nopcs_ctx *c_, cudaStream_t s, int k) : c(c_), st(s), kind(k)
+    {
+        if (!c->profiling) return;
+        if (c->pool_used == c->pool.size()) {
+            cudaStreamSynchronize(st);
+            harvest(c);
+        }
+        pp = &c->pool[c->pool_used++];
+        pp->kind = kind;
+        cudaEventRecord(pp->a, st);
+    }
+    ~Timed()
+    {
+        if (pp) cudaEventRecord(pp->b, st);
+    }
+};
+
+// ---- the RK stage sequence --------------------------------------------------
+template <typename T>
+cudaError_t enqueue_stage(nopcs_ctx *ctx, BoxRes &b, int stage, const double *Qin, T *Rout, cudaStream_t st)
+{
+    const BoxDev &x = b.dev;
+    T *W = (T *)b.W, *R = (T *)b.R;
+    const bool f32 = sizeof(T) == 4;
+    cudaError_t e;
+    {
+        Timed t(ctx, st, K_PREP);
+        e = launch_prep<T>(x, Qin, W, st);
+    }
+    if (e != cudaSuccess) return e;
+    for (int a = 0; a < 3; ++a) {
+        Timed t(ctx, st, K_SX + a);
+        e = launch_line_flux<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, x, W, R, a == 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    double *Qout = stage == 4 ? b.Qn() : b.Qs();
+    {
+        Timed t(ctx, st, K_VISC);
+        e = launch_visc_update<T>(x, W, R, stage, b.Qn(), b.acc(), Qout, Rout, st);
+    }
+    if (e != cudaSuccess || stage == 0) return e;
+    {
+        Timed t(ctx, st, K_BC);
+        e = launch_wall_bc(x, Qout, st, nullptr);
+    }
+    return e;
+}
+
+cudaError_t enqueue_filter(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
+{
+    Timed t(ctx, st, K_FILTER);
+    const BoxDev &x = b.dev;
+    const int bs = b.d.base_subtract;
+    cudaError_t e = launch_line_filter(b.fop[0].dev, 0, x, bs, b.Qn(), b.acc(), st);
+    if (e != cudaSuccess) return e;
+    e = launch_line_filter(b.fop[1].dev, 1, x, bs, b.acc(), b.Qs(), st);
+    if (e != cudaSuccess) return e;
+    return launch_line_filter(b.fop[2].dev, 2, x, bs, b.Qs(), b.Qn(), st);
+}
+
+cudaError_t enqueue_step(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
+{
+    for (int s = 1; s <= 4; ++s) {
+        const double *Qin = s == 1 ? b.Qn() : b.Qs();
+        cudaError_t e = ctx->prec == NOPCS_MIXED ? enqueue_stage<float>(ctx, b, s, Qin, nullptr, st)
+                                                 : enqueue_stage<double>(ctx, b, s, Qin, nullptr, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+nopcs_status check_box(nopcs_ctx *ctx, int box)
+{
+    if (!ctx) return NOPCS_EINVAL;
+    if (box < 0 || box >= (int)ctx->boxes.size()) return fail(ctx, NOPCS_EINVAL, "box index out of range");
+    return NOPCS_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision prec, nopcs_form form,
+                        void *stream, nopcs_ctx **out)
+{
+    if (!out) return fail(nullptr, NOPCS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!boxes || nboxes < 1) return fail(nullptr, NOPCS_EINVAL, "need at least one box");
+    if (prec != NOPCS_FP64 && prec != NOPCS_MIXED) return fail(nullptr, NOPCS_EINVAL, "bad precision");
+    if (form < NOPCS_FORM_AUTO || form > NOPCS_FORM_GEMM_BF16X3) return fail(nullptr, NOPCS_EINVAL, "bad form");
+    for (int i = 0; i < nboxes; ++i) {
+        std::string m;
+        if (!valid_box(boxes[i], m)) return fail(nullptr, NOPCS_EINVAL, "box " + std::to_string(i) + ": " + m);
+    }
+    if (form == NOPCS_FORM_GEMM_3XTF32 || form == NOPCS_FORM_GEMM_BF16X3)
+        return fail(nullptr, NOPCS_EUNSUPPORTED, "GEMM solve forms are not built in this version");
+    nopcs_ctx *ctx = new nopcs_ctx();
+    ctx->prec = prec;
+    ctx->form = NOPCS_FORM_THOMAS;
+    ctx->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = init_line_kernels();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("CUDA: ") + cudaGetErrorString(e);
+        delete ctx;
+        return NOPCS_ECUDA;
+    }
+    ctx->boxes.resize(nboxes);
+    for (int i = 0; i < nboxes; ++i) {
+        ctx->boxes[i].d = boxes[i];
+        if (prec == NOPCS_MIXED) ctx->boxes[i].d.base_subtract = 1;
+        nopcs_status s = setup_box(ctx, ctx->boxes[i]);
+        if (s != NOPCS_OK) {
+            g_init_error = ctx->err;
+            nopcs_destroy(ctx);
+            return s;
+        }
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("initial state: ") + cudaGetErrorString(e);
+        nopcs_destroy(ctx);
+        return NOPCS_ECUDA;
+    }
+    *out = ctx;
+    return NOPCS_OK;
+}
+
+void nopcs_destroy(nopcs_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    for (auto &p : ctx->pool) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto &b : ctx->boxes) free_box(b);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+}
+
+const char *nopcs_last_error(const nopcs_ctx *ctx)
+{
+    if (!ctx) return g_init_error.c_str();
+    return ctx->err.c_str();
+}
+
+nopcs_status nopcs_set_state(nopcs_ctx *ctx, int box, const double *q)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (!q) return fail(ctx, NOPCS_EINVAL, "q is NULL");
+    BoxRes &b = ctx->boxes[box];
+    CK(cudaMemcpyAsync(b.Qn(), q, 5 * (size_t)b.dev.np * sizeof(double), cudaMemcpyDefault, ctx->stream),
+       "set_state");
+    CK(cudaStreamSynchronize(ctx->stream), "set_state");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_get_state(nopcs_ctx *ctx, int box, double *q)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (!q) return fail(ctx, NOPCS_EINVAL, "q is NULL");
+    BoxRes &b = ctx->boxes[box];
+    CK(cudaMemcpyAsync(q, b.Qn(), 5 * (size_t)b.dev.np * sizeof(double), cudaMemcpyDefault, ctx->stream),
+       "get_state");
+    CK(cudaStreamSynchronize(ctx->stream), "get_state");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    BoxRes &b = ctx->boxes[box];
+    CK(launch_initial_state(b.dev, b.d.seed, b.d.perturb_amp, b.Qn(), ctx->stream), "reset_state");
+    b.step = 0;
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int dtype, const void *f, void *df,
+                              void *stream)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (axis < 0 || axis > 2) return fail(ctx, NOPCS_EINVAL, "axis must be 0, 1 or 2");
+    if (order != 1 && order != 2) return fail(ctx, NOPCS_EINVAL, "order must be 1 or 2");
+    if (dtype != 0 && dtype != 1) return fail(ctx, NOPCS_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
+    if (!f || !df) return fail(ctx, NOPCS_EINVAL, "null field pointer");
+    BoxRes &b = ctx->boxes[box];
+    const size_t es = dtype == 0 ? 8 : 4;
+    const size_t bytes = (size_t)b.dev.np * es;
+    const char *fc = (const char *)f, *dc = (const char *)df;
+    if (fc < dc + bytes && dc < fc + bytes) return fail(ctx, NOPCS_EINVAL, "f and df overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double scale = b.dev.inv_h[axis];
+    const LineOpDev &op = dtype == 0 ? b.dop64[axis].dev : b.dop32[axis].dev;
+    const void *src = f;
+    if (order == 2) {
+        if (!b.scratch) {
+            cudaError_t e = cudaMalloc(&b.scratch, (size_t)b.dev.np * 8);
+            if (e != cudaSuccess) {
+                b.scratch = nullptr;
+                return fail(ctx, NOPCS_ENOMEM, "order-2 scratch");
+            }
+        }
+        cudaError_t e = dtype == 0 ? launch_line_field<double>(op, axis, b.dev.n, (const double *)f,
+                                                               (double *)b.scratch, scale, st)
+                                   : launch_line_field<float>(op, axis, b.dev.n, (const float *)f,
+                                                              (float *)b.scratch, scale, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
+        src = b.scratch;
+    }
+    cudaError_t e = dtype == 0 ? launch_line_field<double>(op, axis, b.dev.n, (const double *)src, (double *)df,
+                                                           scale, st)
+                               : launch_line_field<float>(op, axis, b.dev.n, (const float *)src, (float *)df,
+                                                          scale, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps)
+{
+    if (!ctx) return NOPCS_EINVAL;
+    if (nsteps < 0) return fail(ctx, NOPCS_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return NOPCS_OK;
+    if (!ctx->profiling && !ctx->step_exec) {
+        // capture one step of every box once; replayed for every later step
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+        cudaError_t e = cudaSuccess;
+        for (auto &b : ctx->boxes) {
+            e = enqueue_step(ctx, b, ctx->cap_stream);
+            if (e != cudaSuccess) break;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(ctx, e, "graph capture");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "graph capture");
+        e = cudaGraphInstantiate(&ctx->step_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->step_exec = nullptr;
+            return cuda_fail(ctx, e, "graph instantiate");
+        }
+    }
+    for (int it = 0; it < nsteps; ++it) {
+        if (ctx->profiling) {
+            for (auto &b : ctx->boxes) CK(enqueue_step(ctx, b, ctx->stream), "rk step");
+        } else {
+            CK(cudaGraphLaunch(ctx->step_exec, ctx->stream), "graph launch");
+        }
+        for (auto &b : ctx->boxes) {
+            b.step += 1;
+            if (b.d.filter_every > 0 && b.step % b.d.filter_every == 0)
+                CK(enqueue_filter(ctx, b, ctx->stream), "filter");
+        }
+    }
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_rhs(nopcs_ctx *ctx, int box, const double *q, void *r)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (!q || !r) return fail(ctx, NOPCS_EINVAL, "null pointer");
+    BoxRes &b = ctx->boxes[box];
+    cudaError_t e = ctx->prec == NOPCS_MIXED ? enqueue_stage<float>(ctx, b, 0, q, (float *)r, ctx->stream)
+                                             : enqueue_stage<double>(ctx, b, 0, q, (double *)r, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs");
+    CK(cudaStreamSynchronize(ctx->stream), "rhs");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_filter(nopcs_ctx *ctx, int box)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    CK(enqueue_filter(ctx, ctx->boxes[box], ctx->stream), "filter");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (!out) return fail(ctx, NOPCS_EINVAL, "out is NULL");
+    BoxRes &b = ctx->boxes[box];
+    {
+        Timed t(ctx, ctx->stream, K_DIAG);
+        CK(launch_diagnostics(b.dev, b.Qn(), b.partial, b.nblk_diag, b.diag_out, ctx->stream), "diagnostics");
+    }
+    double v[10];
+    CK(cudaMemcpyAsync(v, b.diag_out, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream), "diagnostics");
+    CK(cudaStreamSynchronize(ctx->stream), "diagnostics");
+    out->mass = v[0];
+    out->momentum[0] = v[1];
+    out->momentum[1] = v[2];
+    out->momentum[2] = v[3];
+    out->energy_total = v[4];
+    out->max_speed = v[5];
+    out->max_dp = v[6];
+    out->max_mach = v[7];
+    out->nonfinite = v[8] != 0.0;
+    out->step = b.step;
+    if (out->nonfinite) return fail(ctx, NOPCS_EUNSTABLE, "non-finite values in the state");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_synchronize(nopcs_ctx *ctx)
+{
+    if (!ctx) return NOPCS_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_set_profiling(nopcs_ctx *ctx, int on)
+{
+    if (!ctx) return NOPCS_EINVAL;
+    if (on && ctx->pool.empty()) {
+        ctx->pool.resize(4096);
+        for (auto &p : ctx->pool) {
+            CK(cudaEventCreate(&p.a), "event");
+            CK(cudaEventCreate(&p.b), "event");
+        }
+    }
+    if (!on && ctx->profiling) {
+        CK(cudaStreamSynchronize(ctx->stream), "profiling");
+        harvest(ctx);
+    }
+    ctx->profiling = on != 0;
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_profile_read(nopcs_ctx *ctx, double *ms, long long *launches, int reset)
+{
+    if (!ctx) return NOPCS_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream), "profile read");
+    harvest(ctx);
+    for (int k = 0; k < NOPCS_NUM_KERNELS; ++k) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->prof_n[k];
+        if (reset) {
+            ctx->prof_ms[k] = 0.0;
+            ctx->prof_n[k] = 0;
+        }
+    }
+    return NOPCS_OK;
+}
+
+const char *nopcs_kernel_name(int kind)
+{
+    if (kind < 0 || kind >= NOPCS_NUM_KERNELS) return nullptr;
+    return KERNEL_NAMES[kind];
+}
+
+}  // extern "C"

@@ -1,0 +1,384 @@
+// NOHAP line sweeps on sm_103a (arXiv 2203.00879, Sec. 3).
+//
+// One CUDA block owns one sub-domain [s, e] of LINES neighbouring grid lines.
+// It stages the rows the sub-domain needs (its own points, the end-row
+// supports of up to 48 (FP64) / 24 (FP32) points into the neighbouring
+// sub-domains, and the +-2 (+-3 for the filter) right-hand-side stencil) in
+// shared memory, laid out [field][row][line] with an odd line pitch, so that
+//   - a line along the contiguous x axis is read row-contiguous (coalesced)
+//     and transposed on the fly into the [row][line] layout, and
+//   - lines along y or z are read line-contiguous (coalesced along x).
+// Each thread then owns one (line, field) column and
+//   1. evaluates the two sub-domain end values with the equivalent explicit
+//      rows g_i = sum_j C_ij f_j (Eq. CS:fpCf_i) and any explicit wall-closure
+//      row inside the sub-domain,
+//   2. runs the Thomas forward sweep over the implicit rows (tabulated factors,
+//      the end values moved to the right-hand side) keeping the last 2W+1
+//      inputs in registers and writing the forward values in place,
+//   3. back-substitutes in place.
+// The block finally writes its own rows back (transposed again for x).
+// Sub-domains are independent, so no block waits for another.
+#include "nopcs_internal.cuh"
+
+namespace nopcs {
+
+template <typename T>
+struct LineArgs {
+    int n[3];
+    long long np;
+    int lines;      // lines per block (LINES)
+    int ntile_a;    // tiles along the line-tile axis
+    int rt;         // row capacity of a field column (op.max_tile)
+    const T *in;    // FIELD: f; FLUX: W (6 fields); FILTER: Q (5 fields)
+    T *out;         // FIELD: df; FLUX: R (5 fields); FILTER: Qout (5 fields)
+    T scale;        // 1/h for FIELD and FLUX
+    int first;      // FLUX: store (1) or subtract (0)
+    int ga;         // gravity axis
+    const T *b0;    // FLUX: rho_b, FILTER: rho_b
+    const T *b1;    // FLUX: H_b,   FILTER: E_b
+};
+
+template <typename T>
+__device__ __forceinline__ const T *coef_ptr(const LineOpDev &op);
+template <>
+__device__ __forceinline__ const double *coef_ptr<double>(const LineOpDev &op) { return op.coef64; }
+template <>
+__device__ __forceinline__ const float *coef_ptr<float>(const LineOpDev &op) { return op.coef32; }
+template <typename T>
+__device__ __forceinline__ const T *cp_ptr(const LineOpDev &op);
+template <>
+__device__ __forceinline__ const double *cp_ptr<double>(const LineOpDev &op) { return op.cp64; }
+template <>
+__device__ __forceinline__ const float *cp_ptr<float>(const LineOpDev &op) { return op.cp32; }
+template <typename T>
+__device__ __forceinline__ const T *inv_ptr(const LineOpDev &op);
+template <>
+__device__ __forceinline__ const double *inv_ptr<double>(const LineOpDev &op) { return op.inv64; }
+template <>
+__device__ __forceinline__ const float *inv_ptr<float>(const LineOpDev &op) { return op.inv32; }
+
+template <typename T, int MODE, int AXIS>
+__global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
+    constexpr int W = MODE == MODE_FILTER ? 3 : 2;  // right-hand-side half-width
+    const int LINES = a.lines, LP = a.lines + 1, RT = a.rt;
+    const int nx = a.n[0], ny = a.n[1];
+    const long long np = a.np;
+
+    const int b = blockIdx.x % op.nsub;
+    const int tile = blockIdx.x / op.nsub;
+    const int ta = tile % a.ntile_a;
+    const int cc = tile / a.ntile_a;
+    const int a0 = ta * LINES;
+    const int Na = AXIS == 0 ? ny : nx;
+    const int nl = min(LINES, Na - a0);
+
+    const int *rec = op.sub + b * SUB_REC;
+    const int s = rec[0], e = rec[1], tlo = rec[2], thi = rec[3];
+    const int nrows = thi - tlo + 1;
+    const long long srow = AXIS == 0 ? 1 : (AXIS == 1 ? (long long)nx : (long long)nx * ny);
+    const long long sa = AXIS == 0 ? (long long)nx : 1;
+    const long long sc = AXIS == 2 ? (long long)nx : (long long)nx * ny;
+    const long long gbase = (long long)cc * sc + (long long)a0 * sa;
+    // which of (row, line, cc) is the coordinate along the gravity axis
+    const int gsel = a.ga == AXIS ? 0 : (a.ga == (AXIS == 0 ? 1 : 0) ? 1 : 2);
+
+    // ---- stage rows [tlo, thi] of nl lines -----------------------------------
+    const int total = nrows * nl;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        int r, l;
+        if (AXIS == 0) {
+            r = q % nrows;
+            l = q / nrows;
+        } else {
+            l = q % nl;
+            r = q / nl;
+        }
+        const long long gi = gbase + (long long)(tlo + r) * srow + (long long)l * sa;
+        T *dst = sm + (size_t)r * LP + l;
+        if (MODE == MODE_FIELD) {
+            dst[0] = a.in[gi];
+        } else if (MODE == MODE_FLUX) {
+            const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
+            const T rho = a.b0[gk] + a.in[gi];
+            const T u = a.in[np + gi], v = a.in[2 * np + gi], w = a.in[3 * np + gi];
+            const T pp = a.in[4 * np + gi];
+            const T H = a.b1[gk] + a.in[5 * np + gi];
+            const T ud = AXIS == 0 ? u : (AXIS == 1 ? v : w);
+            const T m = rho * ud;
+            T f1 = m * u, f2 = m * v, f3 = m * w;
+            if (AXIS == 0) f1 += pp;
+            if (AXIS == 1) f2 += pp;
+            if (AXIS == 2) f3 += pp;
+            const size_t fs = (size_t)RT * LP;
+            dst[0] = m;
+            dst[fs] = f1;
+            dst[2 * fs] = f2;
+            dst[3 * fs] = f3;
+            dst[4 * fs] = H * ud;
+        } else {  // FILTER on Q - base
+            const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
+            const size_t fs = (size_t)RT * LP;
+            dst[0] = a.in[gi] - a.b0[gk];
+            dst[fs] = a.in[np + gi];
+            dst[2 * fs] = a.in[2 * np + gi];
+            dst[3 * fs] = a.in[3 * np + gi];
+            dst[4 * fs] = a.in[4 * np + gi] - a.b1[gk];
+        }
+    }
+    __syncthreads();
+
+    // ---- per-(line, field) NOHAP solve ----------------------------------------
+    const int l = threadIdx.x % LINES;
+    const int fld = threadIdx.x / LINES;
+    if (l < nl && fld < NF) {
+        T *col = sm + (size_t)fld * RT * LP + l;
+        auto F = [&](int row) -> T { return col[(size_t)(row - tlo) * LP]; };
+        const T *coef = coef_ptr<T>(op);
+        const int N = op.N, nexp = op.nexp;
+        // 1. end rows from the equivalent explicit scheme
+        T gs = 0, ge = 0;
+        {
+            const int j0 = rec[4], len = rec[5], off = rec[6];
+            T acc = 0;
+            for (int k = 0; k < len; ++k) acc += coef[off + k] * F(j0 + k);
+            gs = acc;
+        }
+        if (rec[8] > 0) {
+            const int j0 = rec[7], len = rec[8], off = rec[9];
+            T acc = 0;
+            for (int k = 0; k < len; ++k) acc += coef[off + k] * F(j0 + k);
+            ge = acc;
+        }
+        // explicit wall-closure rows strictly inside the sub-domain
+        T exL[3] = {0, 0, 0}, exH[3] = {0, 0, 0};
+        for (int r = 0; r < nexp; ++r) {
+            if (r > s && r < e) {
+                T acc = 0;
+                for (int j = 0; j < 5; ++j)
+                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * F(j);
+                exL[r] = acc;
+            }
+            const int rh = N - 1 - r;
+            if (rh > s && rh < e) {
+                T acc = 0;
+                for (int j = 0; j < 5; ++j)
+                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * F(N - 1 - j);
+                exH[r] = (T)op.ex_sign * acc;
+            }
+        }
+        // 2./3. Thomas over the implicit rows lo..hi
+        const int lo = rec[10], hi = rec[11];
+        if (lo <= hi) {
+            const int m = hi - lo + 1;
+            const T al = (T)op.alpha;
+            const T gL = lo == s + 1 ? gs : exL[nexp - 1];
+            const T gR = hi == e - 1 ? ge : exH[nexp - 1];
+            const T *cpp = cp_ptr<T>(op), *ivp = inv_ptr<T>(op);
+            const T r0 = (T)op.rb[0], r1 = (T)op.rb[1], r2 = (T)op.rb[2], r3 = (T)op.rb[3];
+            T win[2 * W + 1];
+#pragma unroll
+            for (int j = 0; j < 2 * W; ++j) win[j] = F(lo - W + j);
+            T dprev = 0;
+            for (int r = 0; r < m; ++r) {
+                const int i = lo + r;
+                win[2 * W] = F(i + W);
+                T rhs;
+                if constexpr (MODE == MODE_FILTER)
+                    rhs = r0 * win[3] + r1 * (win[4] + win[2]) + r2 * (win[5] + win[1]) + r3 * (win[6] + win[0]);
+                else
+                    rhs = r0 * (win[3] - win[1]) + r1 * (win[4] - win[0]);
+                if (r == 0) rhs -= al * gL;
+                if (r == m - 1) rhs -= al * gR;
+                const T dp = (rhs - al * dprev) * ivp[r];
+                col[(size_t)(i - tlo) * LP] = dp;
+                dprev = dp;
+#pragma unroll
+                for (int j = 0; j < 2 * W; ++j) win[j] = win[j + 1];
+            }
+            T x = dprev;
+            for (int r = m - 2; r >= 0; --r) {
+                T *p = col + (size_t)(lo + r - tlo) * LP;
+                x = *p - cpp[r] * x;
+                *p = x;
+            }
+        }
+        // explicit values into their rows
+        col[(size_t)(s - tlo) * LP] = gs;
+        if (rec[8] > 0) col[(size_t)(e - tlo) * LP] = ge;
+        for (int r = 0; r < nexp; ++r) {
+            if (r > s && r < e) col[(size_t)(r - tlo) * LP] = exL[r];
+            const int rh = N - 1 - r;
+            if (rh > s && rh < e) col[(size_t)(rh - tlo) * LP] = exH[r];
+        }
+    }
+    __syncthreads();
+
+    // ---- write the sub-domain's own rows ---------------------------------------
+    const int nown = e - s + 1;
+    const int tot2 = nown * nl;
+    for (int q = threadIdx.x; q < tot2; q += blockDim.x) {
+        int r, ll;
+        if (AXIS == 0) {
+            r = q % nown;
+            ll = q / nown;
+        } else {
+            ll = q % nl;
+            r = q / nl;
+        }
+        const long long gi = gbase + (long long)(s + r) * srow + (long long)ll * sa;
+        const T *src = sm + (size_t)(s - tlo + r) * LP + ll;
+        if (MODE == MODE_FIELD) {
+            a.out[gi] = src[0] * a.scale;
+        } else if (MODE == MODE_FLUX) {
+            const size_t fs = (size_t)RT * LP;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                T v = -src[f * fs] * a.scale;
+                T *o = a.out + f * np + gi;
+                *o = a.first ? v : *o + v;
+            }
+        } else {
+            const int gk = gsel == 0 ? s + r : (gsel == 1 ? a0 + ll : cc);
+            const size_t fs = (size_t)RT * LP;
+            a.out[gi] = src[0] + a.b0[gk];
+            a.out[np + gi] = src[fs];
+            a.out[2 * np + gi] = src[2 * fs];
+            a.out[3 * np + gi] = src[3 * fs];
+            a.out[4 * np + gi] = src[4 * fs] + a.b1[gk];
+        }
+    }
+}
+
+namespace {
+
+constexpr size_t SMEM_BUDGET = 200 * 1024;
+
+int pick_lines(int pref, int rt, int nf, size_t esz)
+{
+    int L = pref;
+    while (L > 1 && (size_t)nf * rt * (L + 1) * esz > SMEM_BUDGET) L /= 2;
+    return L;
+}
+
+template <typename T, int MODE, int AXIS>
+cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cudaStream_t st)
+{
+    constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
+    a.rt = op.max_tile;
+    a.lines = pick_lines(pref_lines, a.rt, NF, sizeof(T));
+    size_t smem = (size_t)NF * a.rt * (a.lines + 1) * sizeof(T);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const int Na = AXIS == 0 ? a.n[1] : a.n[0];
+    const int Nc = AXIS == 2 ? a.n[1] : a.n[2];
+    a.ntile_a = (Na + a.lines - 1) / a.lines;
+    long long nblk = (long long)op.nsub * a.ntile_a * Nc;
+    if (nblk <= 0) return cudaSuccess;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    int threads = a.lines * NF;
+    threads = (threads + 31) / 32 * 32;
+    if (threads > 1024) return cudaErrorInvalidConfiguration;
+    line_kernel<T, MODE, AXIS><<<(unsigned)nblk, threads, smem, st>>>(op, a);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_any(const LineOpDev &op, int axis, LineArgs<T> a, int pref, cudaStream_t st)
+{
+    switch (axis) {
+    case 0: return launch_axis<T, MODE, 0>(op, a, pref, st);
+    case 1: return launch_axis<T, MODE, 1>(op, a, pref, st);
+    case 2: return launch_axis<T, MODE, 2>(op, a, pref, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int MODE, int AXIS>
+cudaError_t allow_smem()
+{
+    return cudaFuncSetAttribute(line_kernel<T, MODE, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                227 * 1024);
+}
+
+}  // namespace
+
+cudaError_t init_line_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    cudaError_t r[] = {
+        allow_smem<float, MODE_FIELD, 0>(),  allow_smem<float, MODE_FIELD, 1>(),  allow_smem<float, MODE_FIELD, 2>(),
+        allow_smem<double, MODE_FIELD, 0>(), allow_smem<double, MODE_FIELD, 1>(), allow_smem<double, MODE_FIELD, 2>(),
+        allow_smem<float, MODE_FLUX, 0>(),   allow_smem<float, MODE_FLUX, 1>(),   allow_smem<float, MODE_FLUX, 2>(),
+        allow_smem<double, MODE_FLUX, 0>(),  allow_smem<double, MODE_FLUX, 1>(),  allow_smem<double, MODE_FLUX, 2>(),
+        allow_smem<double, MODE_FILTER, 0>(), allow_smem<double, MODE_FILTER, 1>(),
+        allow_smem<double, MODE_FILTER, 2>()};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) e = x;
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], const T *f, T *out,
+                              double scale, cudaStream_t st)
+{
+    LineArgs<T> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = n[d];
+    a.np = (long long)n[0] * n[1] * n[2];
+    a.in = f;
+    a.out = out;
+    a.scale = (T)scale;
+    return launch_any<T, MODE_FIELD>(op, axis, a, sizeof(T) == 4 ? 64 : 32, st);
+}
+
+template <typename T>
+cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
+                             int first, cudaStream_t st)
+{
+    LineArgs<T> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
+    a.np = bx.np;
+    a.in = W;
+    a.out = R;
+    a.scale = (T)bx.inv_h[axis];
+    a.first = first;
+    a.ga = bx.ga;
+    if (sizeof(T) == 8) {
+        a.b0 = (const T *)bx.rho_b64;
+        a.b1 = (const T *)bx.H_b64;
+    } else {
+        a.b0 = (const T *)bx.rho_b32;
+        a.b1 = (const T *)bx.H_b32;
+    }
+    return launch_any<T, MODE_FLUX>(op, axis, a, sizeof(T) == 4 ? 32 : 16, st);
+}
+
+cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
+                               const double *Qin, double *Qout, cudaStream_t st)
+{
+    LineArgs<double> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
+    a.np = bx.np;
+    a.in = Qin;
+    a.out = Qout;
+    a.ga = bx.ga;
+    // the base tables hold the hydrostatic state in the base-subtracted form
+    // and zeros in the plain form
+    (void)base_subtract;
+    a.b0 = bx.rho_b64;
+    a.b1 = bx.E_b64;
+    return launch_any<double, MODE_FILTER>(op, axis, a, 16, st);
+}
+
+template cudaError_t launch_line_field<float>(const LineOpDev &, int, const int *, const float *, float *,
+                                              double, cudaStream_t);
+template cudaError_t launch_line_field<double>(const LineOpDev &, int, const int *, const double *,
+                                               double *, double, cudaStream_t);
+template cudaError_t launch_line_flux<float>(const LineOpDev &, int, const BoxDev &, const float *, float *,
+                                             int, cudaStream_t);
+template cudaError_t launch_line_flux<double>(const LineOpDev &, int, const BoxDev &, const double *,
+                                              double *, int, cudaStream_t);
+
+}  // namespace nopcs

@@ -1,0 +1,113 @@
+// Internal declarations shared by the translation units of libnopcs.
+// Nothing here is part of the public ABI (include/nopcs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nopcs.h"
+
+namespace nopcs {
+
+enum LineKind { KIND_DERIV = 0, KIND_FILTER = 1 };
+enum LineMode { MODE_FIELD = 0, MODE_FLUX = 1, MODE_FILTER = 2 };
+
+// Per-sub-domain record of a line operator (ints, device array of nsub * SUB_REC).
+//   [0] s, [1] e            sub-domain rows (inclusive)
+//   [2] tile_lo, [3] tile_hi rows that the block stages in shared memory
+//   [4] j0_s, [5] len_s, [6] off_s   end row at s: first column, taps, offset in coef
+//   [7] j0_e, [8] len_e, [9] off_e   end row at e
+//   [10] lo, [11] hi         implicit rows solved by Thomas (lo > hi: none)
+constexpr int SUB_REC = 12;
+
+// Host copy of a line operator (Sec. 3): partition, end rows, Thomas factors.
+struct LineOpHost {
+    int N = 0, nsub = 0, nexp = 0, kind = 0, sub_n = 0;
+    int maxm = 0, max_tile = 0;
+    double thresh = 0.0, alpha = 0.0;
+    double rb[4] = {0, 0, 0, 0};  // interior right-hand-side weights
+    double ex[3][5] = {};         // explicit rows next to the low wall (taps at 0..4)
+    double ex_sign = 1.0;         // high wall row N-1-r = ex_sign * mirror of row r
+    std::vector<int> sub;         // nsub * SUB_REC
+    std::vector<double> coef;     // end-row taps
+    std::vector<double> cp, inv;  // Thomas factors, maxm entries
+};
+
+// Device view passed by value to the line kernels.
+struct LineOpDev {
+    int N, nsub, nexp, maxm, max_tile;
+    double alpha;
+    double rb[4];
+    double ex[3][5];
+    double ex_sign;
+    const int *sub;
+    const double *coef64;
+    const float *coef32;
+    const double *cp64, *inv64;
+    const float *cp32, *inv32;
+};
+
+// Builds the host tables; returns false (with msg) on bad sizes.
+bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, LineOpHost &op,
+                   std::string &msg);
+int partition_rule(int N, int sub_n, int *start);
+
+// Owns the device copy of a LineOpHost.
+struct LineOpBuf {
+    LineOpHost host;
+    LineOpDev dev{};
+    void *mem = nullptr;
+    cudaError_t upload();
+    void release();
+};
+
+// Physics constants of one box passed by value to kernels.
+struct BoxDev {
+    int n[3];
+    long long np;
+    double h[3], inv_h[3];
+    int ga;            // gravity axis
+    double gamma, gm2, Re, M, kq, suth_S, mub_coef0, mub_coef1, g;
+    double cE;         // 1 / (gamma (gamma - 1) M^2)
+    double dt;
+    const double *rho_b64, *p_b64, *H_b64, *E_b64;  // base tables along ga (zeros if plain)
+    const float *rho_b32, *p_b32, *H_b32;
+    const double *rho_h64, *p_h64;                  // hydrostatic profile (always)
+};
+
+// ---- launchers (line_kernels.cu) -------------------------------------------
+// Raises the dynamic shared-memory limit of every line-kernel instantiation
+// on the current device (called once per context, outside stream capture).
+cudaError_t init_line_kernels();
+// FIELD: out = scale * L f.  T = float or double.
+template <typename T>
+cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], const T *f, T *out,
+                              double scale, cudaStream_t st);
+// FLUX: R (= or -=) L(flux_axis(W)) / h.  first != 0 stores, else subtracts.
+template <typename T>
+cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
+                             int first, cudaStream_t st);
+// FILTER (FP64): Qout = L(Q - base) + base, 5 fields.
+cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
+                               const double *Qin, double *Qout, cudaStream_t st);
+
+// ---- launchers (rk_kernels.cu) ---------------------------------------------
+template <typename T>
+cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st);
+// stage 1..4 of classical RK4, stage 0: R_total written to Rout (rhs only).
+template <typename T>
+cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage,
+                               const double *Qn, double *acc, double *Qout, T *Rout,
+                               cudaStream_t st);
+cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, cudaStream_t st, int *launches);
+cudaError_t launch_initial_state(const BoxDev &bx, unsigned long long seed, double amp, double *Q,
+                                 cudaStream_t st);
+// partial: nblk * 10 doubles scratch; out: 10 doubles (device)
+cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partial, int nblk,
+                               double *out, cudaStream_t st);
+int diag_blocks(long long np);
+
+}  // namespace nopcs

@@ -1,0 +1,357 @@
+// Host construction of the NOHAP line operators (arXiv 2203.00879, Sec. 3).
+//
+// For a line of N nodes the global compact system is [A]{g} = [B]{f}:
+//   derivative (OUCS3, eta = 0): implicit rows 2..N-3 with A = (alpha, 1, alpha),
+//     B = (-b2, -b1, 0, b1, b2) (interior coefficients printed after Eq.
+//     CS:AfpBf; the printed "+-" signs are read as an antisymmetric B), and
+//     explicit wall closures in rows 0, 1, N-2, N-1 (A = identity there);
+//   filter: implicit rows 3..N-4 with A = (alpha_f, 1, alpha_f) and the
+//     symmetric 7-point sixth-order right-hand side; rows 0..2 and N-3..N-1 are
+//     left unfiltered (identity).
+// NOHAP takes every sub-domain end value from the equivalent explicit scheme
+// g_i = sum_j C_ij f_j with C = A^-1 B (Eqs. CS:fpCf, CS:fpCf_i), keeping the
+// taps with |C_ij| >= thresh.  Row i of C is computed here as y^T B with
+// A^T y = e_i: one tridiagonal solve per end row instead of inverting A.
+// The implicit rows between two known values are solved by the Thomas
+// algorithm, whose factors depend only on the position in the run and are
+// tabulated once.
+#include <math.h>
+#include <string.h>
+
+#include "nopcs_internal.cuh"
+
+namespace nopcs {
+
+static const double OUCS3_ALPHA = 0.3793894912;
+static const double OUCS3_B1 = 0.7877868952;
+static const double OUCS3_B2 = 0.045801298;
+static const double WALL_BETA = -0.025;
+
+int partition_rule(int N, int sub_n, int *start)
+{
+    // blocks of sub_n; a remainder of >= 3 points forms its own last block,
+    // a remainder of 1 or 2 points is appended to the previous block
+    if (sub_n <= 0 || sub_n >= N) {
+        start[0] = 0;
+        start[1] = N;
+        return 1;
+    }
+    int full = N / sub_n, rest = N % sub_n;
+    int nb = rest >= 3 ? full + 1 : full;
+    for (int b = 0; b < nb; ++b) start[b] = b * sub_n;
+    start[nb] = N;
+    return nb;
+}
+
+namespace {
+
+struct Banded {
+    // B stored by rows with up to 7 taps: row r covers columns c0[r] .. c0[r] + 6
+    int N;
+    std::vector<int> c0;
+    std::vector<double> w;  // N * 7
+    double at(int r, int c) const
+    {
+        int k = c - c0[r];
+        return (k >= 0 && k < 7) ? w[(size_t)r * 7 + k] : 0.0;
+    }
+};
+
+bool is_explicit(const LineOpHost &op, int i) { return i < op.nexp || i > op.N - 1 - op.nexp; }
+
+// A^T y = e_i for the tridiagonal A of `op` (diagonally dominant: no pivoting).
+void solve_At(const LineOpHost &op, int i, std::vector<double> &y)
+{
+    int N = op.N;
+    // A[r][r-1] = A[r][r+1] = alpha on implicit rows r, 0 otherwise.
+    // (A^T)[r][r-1] = A[r-1][r], (A^T)[r][r+1] = A[r+1][r].
+    std::vector<double> lo(N), di(N), up(N), d(N, 0.0);
+    for (int r = 0; r < N; ++r) {
+        lo[r] = (r > 0 && !is_explicit(op, r - 1)) ? op.alpha : 0.0;
+        up[r] = (r < N - 1 && !is_explicit(op, r + 1)) ? op.alpha : 0.0;
+        di[r] = 1.0;
+    }
+    d[i] = 1.0;
+    for (int r = 1; r < N; ++r) {
+        double m = lo[r] / di[r - 1];
+        di[r] -= m * up[r - 1];
+        d[r] -= m * d[r - 1];
+    }
+    y.assign(N, 0.0);
+    y[N - 1] = d[N - 1] / di[N - 1];
+    for (int r = N - 2; r >= 0; --r) y[r] = (d[r] - up[r] * y[r + 1]) / di[r];
+}
+
+}  // namespace
+
+bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, LineOpHost &op,
+                   std::string &msg)
+{
+    if (N < 5) {
+        msg = "a line needs at least 5 points";
+        return false;
+    }
+    if (sub_n > 0 && sub_n < 3) {
+        msg = "sub-domain length must be >= 3 (or 0 for a single sub-domain)";
+        return false;
+    }
+    if (!(thresh > 0.0)) {
+        msg = "truncation threshold must be positive";
+        return false;
+    }
+    op = LineOpHost();
+    op.N = N;
+    op.kind = kind;
+    op.sub_n = sub_n;
+    op.thresh = thresh;
+    Banded B;
+    B.N = N;
+    B.c0.assign(N, 0);
+    B.w.assign((size_t)N * 7, 0.0);
+    auto setB = [&](int r, int c, double v) {
+        int k = c - B.c0[r];
+        B.w[(size_t)r * 7 + k] = v;
+    };
+    int w;  // half-width of the interior right-hand side
+    if (kind == KIND_DERIV) {
+        op.nexp = 2;
+        op.alpha = OUCS3_ALPHA;
+        op.rb[0] = OUCS3_B1;
+        op.rb[1] = OUCS3_B2;
+        w = 2;
+        // wall closure rows (explicit): one-sided second order at the wall, the
+        // fourth-order beta family next to it; mirrored antisymmetrically
+        const double be = WALL_BETA;
+        const double r0[5] = {-1.5, 2.0, -0.5, 0.0, 0.0};
+        const double r1[5] = {2.0 * be / 3.0 - 1.0 / 3.0, -(8.0 * be / 3.0 + 0.5), 4.0 * be + 1.0,
+                              -(8.0 * be / 3.0 + 1.0 / 6.0), 2.0 * be / 3.0};
+        for (int j = 0; j < 5; ++j) {
+            op.ex[0][j] = r0[j];
+            op.ex[1][j] = r1[j];
+        }
+        op.ex_sign = -1.0;
+    } else {
+        op.nexp = 3;
+        op.alpha = alpha_f;
+        const double af = alpha_f;
+        op.rb[0] = (11.0 + 10.0 * af) / 16.0;
+        op.rb[1] = 0.5 * (15.0 + 34.0 * af) / 32.0;
+        op.rb[2] = 0.5 * (-3.0 + 6.0 * af) / 16.0;
+        op.rb[3] = 0.5 * (1.0 - 2.0 * af) / 32.0;
+        w = 3;
+        for (int r = 0; r < 3; ++r) op.ex[r][r] = 1.0;
+        op.ex_sign = 1.0;
+    }
+    // banded B
+    for (int r = 0; r < N; ++r) {
+        if (r < op.nexp) {
+            B.c0[r] = 0;
+            for (int j = 0; j < 5 && j < N; ++j) setB(r, j, op.ex[r][j]);
+        } else if (r > N - 1 - op.nexp) {
+            int rr = N - 1 - r;
+            B.c0[r] = N - 7 < 0 ? 0 : N - 7;
+            for (int j = 0; j < 5; ++j)
+                if (op.ex[rr][j] != 0.0) setB(r, N - 1 - j, op.ex_sign * op.ex[rr][j]);
+        } else {
+            B.c0[r] = r - 3;
+            if (kind == KIND_DERIV) {
+                setB(r, r - 2, -op.rb[1]);
+                setB(r, r - 1, -op.rb[0]);
+                setB(r, r + 1, op.rb[0]);
+                setB(r, r + 2, op.rb[1]);
+            } else {
+                setB(r, r, op.rb[0]);
+                for (int k = 1; k <= 3; ++k) {
+                    setB(r, r - k, op.rb[k]);
+                    setB(r, r + k, op.rb[k]);
+                }
+            }
+        }
+    }
+    // partition and end rows
+    std::vector<int> start(N + 2);
+    op.nsub = partition_rule(N, sub_n, start.data());
+    op.sub.assign((size_t)op.nsub * SUB_REC, 0);
+    std::vector<double> y, crow(N);
+    auto end_row = [&](int i, int &j0, int &len) {
+        j0 = op.coef.size();  // placeholder
+        if (is_explicit(op, i)) {
+            // explicit rows are their own C rows
+            int a = N, b = -1;
+            for (int j = 0; j < N; ++j)
+                if (B.at(i, j) != 0.0) {
+                    a = j < a ? j : a;
+                    b = j;
+                }
+            j0 = a;
+            len = b - a + 1;
+            for (int j = a; j <= b; ++j) op.coef.push_back(B.at(i, j));
+            return;
+        }
+        solve_At(op, i, y);
+        for (int j = 0; j < N; ++j) crow[j] = 0.0;
+        for (int r = 0; r < N; ++r) {
+            if (y[r] == 0.0) continue;
+            for (int k = 0; k < 7; ++k) {
+                int c = B.c0[r] + k;
+                if (c >= 0 && c < N) crow[c] += y[r] * B.w[(size_t)r * 7 + k];
+            }
+        }
+        int a = N, b = -1;
+        for (int j = 0; j < N; ++j)
+            if (fabs(crow[j]) >= thresh) {
+                a = j < a ? j : a;
+                b = j;
+            }
+        if (b < a) {
+            a = i;
+            b = i;
+        }
+        j0 = a;
+        len = b - a + 1;
+        for (int j = a; j <= b; ++j) op.coef.push_back(fabs(crow[j]) >= thresh ? crow[j] : 0.0);
+    };
+    for (int b = 0; b < op.nsub; ++b) {
+        int *rec = &op.sub[(size_t)b * SUB_REC];
+        int s = start[b], e = start[b + 1] - 1;
+        rec[0] = s;
+        rec[1] = e;
+        int j0, len;
+        rec[6] = (int)op.coef.size();
+        end_row(s, j0, len);
+        rec[4] = j0;
+        rec[5] = len;
+        if (e != s) {
+            rec[9] = (int)op.coef.size();
+            end_row(e, j0, len);
+            rec[7] = j0;
+            rec[8] = len;
+        } else {
+            rec[7] = rec[4];
+            rec[8] = 0;
+            rec[9] = rec[6];
+        }
+        int lo = s + 1 > op.nexp ? s + 1 : op.nexp;
+        int hi = e - 1 < N - 1 - op.nexp ? e - 1 : N - 1 - op.nexp;
+        rec[10] = lo;
+        rec[11] = hi;
+        // rows the block must stage
+        int tlo = s, thi = e;
+        auto cover = [&](int a, int c) {
+            if (a < tlo) tlo = a;
+            if (c > thi) thi = c;
+        };
+        cover(rec[4], rec[4] + rec[5] - 1);
+        if (rec[8] > 0) cover(rec[7], rec[7] + rec[8] - 1);
+        if (lo <= hi) cover(lo - w, hi + w);
+        for (int r = 0; r < op.nexp; ++r) {
+            if (r > s && r < e) cover(0, 4 < N - 1 ? 4 : N - 1);
+            if (N - 1 - r > s && N - 1 - r < e) cover(N - 5 > 0 ? N - 5 : 0, N - 1);
+        }
+        if (tlo < 0) tlo = 0;
+        if (thi > N - 1) thi = N - 1;
+        rec[2] = tlo;
+        rec[3] = thi;
+        int m = hi - lo + 1;
+        if (m > op.maxm) op.maxm = m;
+        if (thi - tlo + 1 > op.max_tile) op.max_tile = thi - tlo + 1;
+    }
+    // Thomas factors for a run of implicit rows after a known value
+    int mm = op.maxm > 0 ? op.maxm : 1;
+    op.cp.assign(mm, 0.0);
+    op.inv.assign(mm, 0.0);
+    for (int r = 0; r < mm; ++r) {
+        double den = r == 0 ? 1.0 : 1.0 - op.alpha * op.cp[r - 1];
+        op.inv[r] = 1.0 / den;
+        op.cp[r] = op.alpha * op.inv[r];
+    }
+    return true;
+}
+
+cudaError_t LineOpBuf::upload()
+{
+    release();
+    const LineOpHost &h = host;
+    size_t nsub_b = h.sub.size() * sizeof(int);
+    size_t nc = h.coef.size() > 0 ? h.coef.size() : 1;
+    size_t nm = h.cp.size();
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o_sub = 0, o_c64 = al(nsub_b), o_c32 = o_c64 + al(nc * 8), o_cp64 = o_c32 + al(nc * 4),
+           o_inv64 = o_cp64 + al(nm * 8), o_cp32 = o_inv64 + al(nm * 8), o_inv32 = o_cp32 + al(nm * 4),
+           tot = o_inv32 + al(nm * 4);
+    cudaError_t e = cudaMalloc(&mem, tot);
+    if (e != cudaSuccess) {
+        mem = nullptr;
+        return e;
+    }
+    std::vector<char> stage(tot, 0);
+    memcpy(stage.data() + o_sub, h.sub.data(), nsub_b);
+    for (size_t i = 0; i < h.coef.size(); ++i) {
+        ((double *)(stage.data() + o_c64))[i] = h.coef[i];
+        ((float *)(stage.data() + o_c32))[i] = (float)h.coef[i];
+    }
+    for (size_t i = 0; i < nm; ++i) {
+        ((double *)(stage.data() + o_cp64))[i] = h.cp[i];
+        ((double *)(stage.data() + o_inv64))[i] = h.inv[i];
+        ((float *)(stage.data() + o_cp32))[i] = (float)h.cp[i];
+        ((float *)(stage.data() + o_inv32))[i] = (float)h.inv[i];
+    }
+    e = cudaMemcpy(mem, stage.data(), tot, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    char *b = (char *)mem;
+    dev.N = h.N;
+    dev.nsub = h.nsub;
+    dev.nexp = h.nexp;
+    dev.maxm = h.maxm;
+    dev.max_tile = h.max_tile;
+    dev.alpha = h.alpha;
+    for (int i = 0; i < 4; ++i) dev.rb[i] = h.rb[i];
+    memcpy(dev.ex, h.ex, sizeof(dev.ex));
+    dev.ex_sign = h.ex_sign;
+    dev.sub = (const int *)(b + o_sub);
+    dev.coef64 = (const double *)(b + o_c64);
+    dev.coef32 = (const float *)(b + o_c32);
+    dev.cp64 = (const double *)(b + o_cp64);
+    dev.inv64 = (const double *)(b + o_inv64);
+    dev.cp32 = (const float *)(b + o_cp32);
+    dev.inv32 = (const float *)(b + o_inv32);
+    return cudaSuccess;
+}
+
+void LineOpBuf::release()
+{
+    if (mem) cudaFree(mem);
+    mem = nullptr;
+}
+
+}  // namespace nopcs
+
+using namespace nopcs;
+
+extern "C" nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double alpha_f, double thresh,
+                                            int *nsub, int *starts, int *end_j0, int *end_len,
+                                            double *coef, int max_coef)
+{
+    if (kind != KIND_DERIV && kind != KIND_FILTER) return NOPCS_EINVAL;
+    LineOpHost op;
+    std::string msg;
+    if (!build_line_op(N, sub_n, kind, alpha_f, thresh, op, msg)) return NOPCS_EINVAL;
+    if ((int)op.coef.size() > max_coef) return NOPCS_EINVAL;
+    if (nsub) *nsub = op.nsub;
+    for (int b = 0; b < op.nsub; ++b) {
+        const int *rec = &op.sub[(size_t)b * SUB_REC];
+        if (starts) starts[b] = rec[0];
+        if (end_j0) {
+            end_j0[2 * b] = rec[4];
+            end_j0[2 * b + 1] = rec[7];
+        }
+        if (end_len) {
+            end_len[2 * b] = rec[5];
+            end_len[2 * b + 1] = rec[8];
+        }
+    }
+    if (starts) starts[op.nsub] = N;
+    if (coef)
+        for (size_t i = 0; i < op.coef.size(); ++i) coef[i] = op.coef[i];
+    return NOPCS_OK;
+}

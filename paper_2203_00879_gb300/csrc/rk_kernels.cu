@@ -1,0 +1,543 @@
+// Point-wise and stencil kernels of one RK stage (arXiv 2203.00879, Sec. 2 and
+// Sec. 4): primitive recovery, the second-order explicit viscous terms with
+// bulk viscosity, the gravity source, the classical RK4 stage update in FP64,
+// the no-slip adiabatic wall conditions, the initial state and the
+// diagnostics reduction.
+#include <math.h>
+
+#include "nopcs_internal.cuh"
+
+namespace nopcs {
+
+namespace {
+
+
+__device__ __forceinline__ void coords(const BoxDev &bx, long long p, int c[3])
+{
+    c[0] = (int)(p % bx.n[0]);
+    long long q = p / bx.n[0];
+    c[1] = (int)(q % bx.n[1]);
+    c[2] = (int)(q / bx.n[1]);
+}
+
+template <typename T>
+struct Base;
+template <>
+struct Base<double> {
+    static __device__ __forceinline__ const double *rho(const BoxDev &b) { return b.rho_b64; }
+    static __device__ __forceinline__ const double *p(const BoxDev &b) { return b.p_b64; }
+};
+template <>
+struct Base<float> {
+    static __device__ __forceinline__ const float *rho(const BoxDev &b) { return b.rho_b32; }
+    static __device__ __forceinline__ const float *p(const BoxDev &b) { return b.p_b32; }
+};
+
+// ---------------------------------------------------------------------------
+// Primitive recovery (Eqs. ge12, ge13, nondimensional): from the FP64 state to
+// W = (rho - rho_b, u, v, w, p - p_b, E + p - H_b) in the compute precision,
+// with (rho_b, p_b, H_b) the hydrostatic base in the base-subtracted form and
+// zero in the plain form.  The mixed form takes the two large differences
+// rho - rho_b and E - E_b in FP64 and the rest in FP32, using
+// p - p_b = (gamma - 1)(E - E_b - rho |V|^2 / 2) and H - H_b = (E - E_b) + (p - p_b).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void prep_kernel(const BoxDev bx, const double *__restrict__ Q, T *__restrict__ W)
+{
+    const long long np = bx.np;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coords(bx, p, c);
+        const int kg = c[bx.ga];
+        const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
+        if constexpr (sizeof(T) == 8) {
+            const double u = mx / r, v = my / r, w = mz / r;
+            const double pr = (bx.gamma - 1.0) * (E - 0.5 * (mx * u + my * v + mz * w));
+            W[p] = r - bx.rho_b64[kg];
+            W[np + p] = u;
+            W[2 * np + p] = v;
+            W[3 * np + p] = w;
+            W[4 * np + p] = pr - bx.p_b64[kg];
+            W[5 * np + p] = E + pr - bx.H_b64[kg];
+        } else {
+            const float rd = (float)(r - bx.rho_b64[kg]);
+            const float Ed = (float)(E - bx.E_b64[kg]);
+            const float rf = (float)r;
+            const float ir = 1.0f / rf;
+            const float u = (float)mx * ir, v = (float)my * ir, w = (float)mz * ir;
+            const float ke = 0.5f * rf * (u * u + v * v + w * w);
+            const float pd = (float)(bx.gamma - 1.0) * (Ed - ke);
+            W[p] = rd;
+            W[np + p] = u;
+            W[2 * np + p] = v;
+            W[3 * np + p] = w;
+            W[4 * np + p] = pd;
+            W[5 * np + p] = Ed + pd;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Viscous terms (Sec. 4: second-order explicit), Eqs. ge19, bv1-bv3, ge20.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Visc {
+    const T *W;
+    long long np;
+    int n[3];
+    long long st[3];
+    T ih2[3];  // 1 / (2 h)
+    const T *rho_b, *p_b;
+    int ga;
+    T gm2, iRe, kq, S1, S, c0, c1;
+
+    __device__ __forceinline__ int gk(const int c[3]) const { return c[ga]; }
+    __device__ __forceinline__ T vel(int a, long long i) const { return W[(1 + a) * np + i]; }
+    __device__ __forceinline__ T temp(long long i, int kg) const
+    {
+        return gm2 * (p_b[kg] + W[4 * np + i]) / (rho_b[kg] + W[i]);
+    }
+    // derivative along axis a at node (coordinate ca, index i) of field f(i)
+    template <class Fn>
+    __device__ __forceinline__ T d1(int a, int ca, long long i, Fn f) const
+    {
+        const long long s = st[a];
+        if (ca == 0) return (T(-3) * f(i) + T(4) * f(i + s) - f(i + 2 * s)) * ih2[a];
+        if (ca == n[a] - 1) return (T(3) * f(i) - T(4) * f(i - s) + f(i - 2 * s)) * ih2[a];
+        return (f(i + s) - f(i - s)) * ih2[a];
+    }
+    // nodal viscous flux along axis d at node (c, i): tau_d0, tau_d1, tau_d2,
+    // u_a tau_da - q_d (q_d = 0 on a wall normal to d)
+    __device__ void flux(int d, const int c[3], long long i, T out[4]) const
+    {
+        const int kg0 = gk(c);
+        const T Tn = temp(i, kg0);
+        const T mu = Tn * sqrt(Tn) * S1 / (Tn + S);
+        const T mub = c0 * Tn + c1;
+        T gd[3];  // d u_a / d x_d
+        T ga_[3]; // d u_a / d x_a
+        T gx[3];  // d u_d / d x_a
+        for (int a = 0; a < 3; ++a) gd[a] = d1(d, c[d], i, [&](long long j) { return vel(a, j); });
+        for (int a = 0; a < 3; ++a) {
+            if (a == d) {
+                ga_[a] = gd[a];
+                gx[a] = gd[a];
+                continue;
+            }
+            ga_[a] = d1(a, c[a], i, [&](long long j) { return vel(a, j); });
+            gx[a] = d1(a, c[a], i, [&](long long j) { return vel(d, j); });
+        }
+        const T div = ga_[0] + ga_[1] + ga_[2];
+        T tau[3];
+        for (int a = 0; a < 3; ++a) {
+            if (a == d)
+                tau[a] = ((T(4) / T(3) * mu + mub) * gd[d] + (T(-2) / T(3) * mu + mub) * (div - gd[d])) * iRe;
+            else
+                tau[a] = mu * iRe * (gd[a] + gx[a]);
+        }
+        T q = T(0);
+        if (c[d] != 0 && c[d] != n[d] - 1) {
+            int cc[3] = {c[0], c[1], c[2]};
+            const T dT = d1(d, c[d], i, [&](long long j) {
+                // coordinate along the gravity axis of node j on the d-line
+                int off = (int)((j - i) / st[d]);
+                cc[d] = c[d] + off;
+                T t = temp(j, gk(cc));
+                cc[d] = c[d];
+                return t;
+            });
+            q = -mu * kq * dT;
+        }
+        out[0] = tau[0];
+        out[1] = tau[1];
+        out[2] = tau[2];
+        out[3] = vel(0, i) * tau[0] + vel(1, i) * tau[1] + vel(2, i) * tau[2] - q;
+    }
+};
+
+// R_total = R + div(viscous flux) + S, then the RK4 stage (stage 1..4) in FP64,
+// or (stage 0) R_total stored to Rout.
+template <typename T>
+__global__ void visc_update_kernel(const BoxDev bx, const Visc<T> V, const T *__restrict__ R, int stage,
+                                   const double *__restrict__ Qn, double *__restrict__ acc,
+                                   double *__restrict__ Qout, T *__restrict__ Rout)
+{
+    const long long np = bx.np;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coords(bx, p, c);
+        T r[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = R[k * np + p];
+        // divergence of the nodal viscous fluxes, same explicit operator
+        for (int d = 0; d < 3; ++d) {
+            const long long s = V.st[d];
+            T fa[4], fb[4], fc[4];
+            int cn[3] = {c[0], c[1], c[2]};
+            T dv[4];
+            if (c[d] == 0) {
+                V.flux(d, cn, p, fa);
+                cn[d] = 1;
+                V.flux(d, cn, p + s, fb);
+                cn[d] = 2;
+                V.flux(d, cn, p + 2 * s, fc);
+                for (int k = 0; k < 4; ++k) dv[k] = (T(-3) * fa[k] + T(4) * fb[k] - fc[k]) * V.ih2[d];
+            } else if (c[d] == bx.n[d] - 1) {
+                V.flux(d, cn, p, fa);
+                cn[d] = c[d] - 1;
+                V.flux(d, cn, p - s, fb);
+                cn[d] = c[d] - 2;
+                V.flux(d, cn, p - 2 * s, fc);
+                for (int k = 0; k < 4; ++k) dv[k] = (T(3) * fa[k] - T(4) * fb[k] + fc[k]) * V.ih2[d];
+            } else {
+                cn[d] = c[d] + 1;
+                V.flux(d, cn, p + s, fa);
+                cn[d] = c[d] - 1;
+                V.flux(d, cn, p - s, fb);
+                for (int k = 0; k < 4; ++k) dv[k] = (fa[k] - fb[k]) * V.ih2[d];
+            }
+            for (int k = 0; k < 4; ++k) r[1 + k] += dv[k];
+        }
+        // gravity source, Eq. ge8a: -(rho - rho_b) g in the momentum equation
+        // along the gravity axis, -rho u_g g in the energy equation
+        const int kg = c[bx.ga];
+        const T W0 = V.W[p];
+        const T rho = Base<T>::rho(bx)[kg] + W0;
+        const T ug = V.W[(1 + bx.ga) * np + p];
+        r[1 + bx.ga] -= W0 * (T)bx.g;
+        r[4] -= rho * ug * (T)bx.g;
+        // no-slip: momentum is held at zero on the walls
+        const bool wall = c[0] == 0 || c[0] == bx.n[0] - 1 || c[1] == 0 || c[1] == bx.n[1] - 1 || c[2] == 0 ||
+                          c[2] == bx.n[2] - 1;
+        if (wall) r[1] = r[2] = r[3] = T(0);
+        if (stage == 0) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Rout[k * np + p] = r[k];
+            continue;
+        }
+        const double dt = bx.dt;
+        // classical RK4: acc accumulates Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
+        const double bw = (stage == 1 || stage == 4) ? dt / 6.0 : dt / 3.0;
+        const double cw = stage == 3 ? dt : 0.5 * dt;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const double rk = (double)r[k];
+            const long long o = k * np + p;
+            if (stage == 1) {
+                const double q = Qn[o];
+                acc[o] = q + bw * rk;
+                Qout[o] = q + cw * rk;
+            } else if (stage < 4) {
+                acc[o] = acc[o] + bw * rk;
+                Qout[o] = Qn[o] + cw * rk;
+            } else {
+                Qout[o] = acc[o] + bw * rk;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// No-slip adiabatic walls: momentum zero on every wall node (kept by the
+// update), T_w = (4 T_1 - T_2) / 3 along the inward normal, averaged over the
+// normals of edge and corner nodes; faces first, then edges from the faces,
+// then corners from the edges.  E_w = rho_w T_w / (gamma (gamma-1) M^2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double temp_q(const BoxDev &bx, const double *Q, long long i)
+{
+    const long long np = bx.np;
+    const double r = Q[i];
+    const double ke = 0.5 * (Q[np + i] * Q[np + i] + Q[2 * np + i] * Q[2 * np + i] + Q[3 * np + i] * Q[3 * np + i]) / r;
+    return bx.gm2 * (bx.gamma - 1.0) * (Q[4 * np + i] - ke) / r;
+}
+
+__device__ void set_wall_node(const BoxDev &bx, double *Q, const int c[3])
+{
+    const long long st[3] = {1, bx.n[0], (long long)bx.n[0] * bx.n[1]};
+    const long long i = c[0] + st[1] * c[1] + st[2] * c[2];
+    double Tw = 0.0;
+    int nw = 0;
+    for (int d = 0; d < 3; ++d) {
+        long long s;
+        if (c[d] == 0)
+            s = st[d];
+        else if (c[d] == bx.n[d] - 1)
+            s = -st[d];
+        else
+            continue;
+        Tw += (4.0 * temp_q(bx, Q, i + s) - temp_q(bx, Q, i + 2 * s)) / 3.0;
+        ++nw;
+    }
+    Tw /= nw;
+    const long long np = bx.np;
+    Q[np + i] = Q[2 * np + i] = Q[3 * np + i] = 0.0;
+    Q[4 * np + i] = Q[i] * Tw * bx.cE;
+}
+
+// face nodes: exactly one wall coordinate
+__global__ void wall_face_kernel(const BoxDev bx, double *Q)
+{
+    const int nx = bx.n[0], ny = bx.n[1], nz = bx.n[2];
+    const long long fx = (long long)(ny - 2) * (nz - 2), fy = (long long)(nx - 2) * (nz - 2),
+                    fz = (long long)(nx - 2) * (ny - 2);
+    const long long tot = 2 * (fx + fy + fz);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        long long q = t;
+        if (q < 2 * fx) {
+            int side = (int)(q / fx);
+            q %= fx;
+            c[0] = side ? nx - 1 : 0;
+            c[1] = 1 + (int)(q % (ny - 2));
+            c[2] = 1 + (int)(q / (ny - 2));
+        } else if ((q -= 2 * fx) < 2 * fy) {
+            int side = (int)(q / fy);
+            q %= fy;
+            c[1] = side ? ny - 1 : 0;
+            c[0] = 1 + (int)(q % (nx - 2));
+            c[2] = 1 + (int)(q / (nx - 2));
+        } else {
+            q -= 2 * fy;
+            int side = (int)(q / fz);
+            q %= fz;
+            c[2] = side ? nz - 1 : 0;
+            c[0] = 1 + (int)(q % (nx - 2));
+            c[1] = 1 + (int)(q / (nx - 2));
+        }
+        set_wall_node(bx, Q, c);
+    }
+}
+
+// edges (two wall coordinates), then corners; one block
+__global__ void wall_edge_corner_kernel(const BoxDev bx, double *Q)
+{
+    const int n[3] = {bx.n[0], bx.n[1], bx.n[2]};
+    // edge along axis a: the other two axes at 0 or n-1 (4 combinations)
+    long long cnt[3];
+    for (int a = 0; a < 3; ++a) cnt[a] = 4LL * (n[a] - 2);
+    const long long tot = cnt[0] + cnt[1] + cnt[2];
+    for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+        long long q = t;
+        int a = 0;
+        while (q >= cnt[a]) {
+            q -= cnt[a];
+            ++a;
+        }
+        const int combo = (int)(q / (n[a] - 2));
+        const int along = 1 + (int)(q % (n[a] - 2));
+        const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+        int c[3];
+        c[a] = along;
+        c[b1] = (combo & 1) ? n[b1] - 1 : 0;
+        c[b2] = (combo & 2) ? n[b2] - 1 : 0;
+        set_wall_node(bx, Q, c);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        int c[3];
+        for (int d = 0; d < 3; ++d) c[d] = (threadIdx.x >> d) & 1 ? n[d] - 1 : 0;
+        set_wall_node(bx, Q, c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (Sec. 2, Fig. 1): quiescent hydrostatic two-temperature box
+// plus a uniform velocity perturbation from SplitMix64 (Steele, Lea & Flood,
+// 2014) used as a counter-based generator, value 3 p + component.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long c)
+{
+    unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void initial_state_kernel(const BoxDev bx, unsigned long long seed, double amp, double *Q)
+{
+    const long long np = bx.np;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coords(bx, p, c);
+        const int kg = c[bx.ga];
+        const double rho = bx.rho_h64[kg], pr = bx.p_h64[kg];
+        double V[3] = {0.0, 0.0, 0.0};
+        const bool wall = c[0] == 0 || c[0] == bx.n[0] - 1 || c[1] == 0 || c[1] == bx.n[1] - 1 || c[2] == 0 ||
+                          c[2] == bx.n[2] - 1;
+        if (!wall && amp != 0.0) {
+            for (int k = 0; k < 3; ++k) {
+                const unsigned long long z = splitmix64_at(seed, 3ull * (unsigned long long)p + k);
+                const double U = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+                V[k] = amp * (2.0 * U - 1.0);
+            }
+        }
+        Q[p] = rho;
+        Q[np + p] = rho * V[0];
+        Q[2 * np + p] = rho * V[1];
+        Q[3 * np + p] = rho * V[2];
+        Q[4 * np + p] = pr / (bx.gamma - 1.0) + 0.5 * rho * (V[0] * V[0] + V[1] * V[1] + V[2] * V[2]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: per-block partials (fixed grid, fixed order), then one block.
+// partial record: mass, mx, my, mz, energy, max|V|, max|dp|, max Mach, bad
+// ---------------------------------------------------------------------------
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_REC = 10;
+
+__global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ Q, double *partial)
+{
+    __shared__ double sh[DIAG_REC][DIAG_THREADS];
+    const long long np = bx.np;
+    double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coords(bx, p, c);
+        const int kg = c[bx.ga];
+        const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
+        const bool bad = !isfinite(r) || !isfinite(mx) || !isfinite(my) || !isfinite(mz) || !isfinite(E);
+        if (bad) v[8] = 1.0;
+        v[0] += r;
+        v[1] += mx;
+        v[2] += my;
+        v[3] += mz;
+        v[4] += E + r * bx.g * (kg * bx.h[bx.ga]);
+        const double u = mx / r, vv = my / r, w = mz / r;
+        const double sp = sqrt(u * u + vv * vv + w * w);
+        const double pr = (bx.gamma - 1.0) * (E - 0.5 * r * sp * sp);
+        const double T = bx.gm2 * pr / r;
+        v[5] = fmax(v[5], sp);
+        v[6] = fmax(v[6], fabs(pr - bx.p_h64[kg]));
+        v[7] = fmax(v[7], sp * bx.M / sqrt(T));
+    }
+    for (int k = 0; k < DIAG_REC; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+            for (int k = 5; k < 9; ++k) sh[k][threadIdx.x] = fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < DIAG_REC) partial[(size_t)blockIdx.x * DIAG_REC + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void diag_final_kernel(const BoxDev bx, const double *partial, int nblk, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblk; ++b) {
+        const double *q = partial + (size_t)b * DIAG_REC;
+        for (int k = 0; k < 5; ++k) v[k] += q[k];
+        for (int k = 5; k < 9; ++k) v[k] = fmax(v[k], q[k]);
+    }
+    const double dV = bx.h[0] * bx.h[1] * bx.h[2];
+    for (int k = 0; k < 5; ++k) v[k] *= dV;
+    for (int k = 0; k < DIAG_REC; ++k) out[k] = v[k];
+}
+
+template <typename T>
+Visc<T> make_visc(const BoxDev &bx, const T *W)
+{
+    Visc<T> V;
+    V.W = W;
+    V.np = bx.np;
+    for (int d = 0; d < 3; ++d) V.n[d] = bx.n[d];
+    V.st[0] = 1;
+    V.st[1] = bx.n[0];
+    V.st[2] = (long long)bx.n[0] * bx.n[1];
+    for (int d = 0; d < 3; ++d) V.ih2[d] = (T)(0.5 * bx.inv_h[d]);
+    if constexpr (sizeof(T) == 8) {
+        V.rho_b = (const T *)bx.rho_b64;
+        V.p_b = (const T *)bx.p_b64;
+    } else {
+        V.rho_b = (const T *)bx.rho_b32;
+        V.p_b = (const T *)bx.p_b32;
+    }
+    V.ga = bx.ga;
+    V.gm2 = (T)bx.gm2;
+    V.iRe = (T)(1.0 / bx.Re);
+    V.kq = (T)bx.kq;
+    V.S1 = (T)(1.0 + bx.suth_S);
+    V.S = (T)bx.suth_S;
+    V.c0 = (T)bx.mub_coef0;
+    V.c1 = (T)bx.mub_coef1;
+    return V;
+}
+
+int grid_for(long long work, int threads)
+{
+    long long b = (work + threads - 1) / threads;
+    const long long cap = 152LL * 16;  // grid-stride beyond 16 blocks per SM
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st)
+{
+    prep_kernel<T><<<grid_for(bx.np, 256), 256, 0, st>>>(bx, Q, W);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const double *Qn,
+                               double *acc, double *Qout, T *Rout, cudaStream_t st)
+{
+    Visc<T> V = make_visc<T>(bx, W);
+    visc_update_kernel<T><<<grid_for(bx.np, 128), 128, 0, st>>>(bx, V, R, stage, Qn, acc, Qout, Rout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, cudaStream_t st, int *launches)
+{
+    const long long faces = 2LL * ((long long)(bx.n[1] - 2) * (bx.n[2] - 2) + (long long)(bx.n[0] - 2) * (bx.n[2] - 2) +
+                                   (long long)(bx.n[0] - 2) * (bx.n[1] - 2));
+    wall_face_kernel<<<grid_for(faces, 256), 256, 0, st>>>(bx, Q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wall_edge_corner_kernel<<<1, 512, 0, st>>>(bx, Q);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_initial_state(const BoxDev &bx, unsigned long long seed, double amp, double *Q,
+                                 cudaStream_t st)
+{
+    initial_state_kernel<<<grid_for(bx.np, 256), 256, 0, st>>>(bx, seed, amp, Q);
+    return cudaGetLastError();
+}
+
+int diag_blocks(long long np)
+{
+    long long b = (np + DIAG_THREADS - 1) / DIAG_THREADS;
+    return b > 1024 ? 1024 : (int)b;
+}
+
+cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partial, int nblk, double *out,
+                               cudaStream_t st)
+{
+    diag_partial_kernel<<<nblk, DIAG_THREADS, 0, st>>>(bx, Q, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<<<1, 32, 0, st>>>(bx, partial, nblk, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_prep<float>(const BoxDev &, const double *, float *, cudaStream_t);
+template cudaError_t launch_prep<double>(const BoxDev &, const double *, double *, cudaStream_t);
+template cudaError_t launch_visc_update<float>(const BoxDev &, const float *, const float *, int,
+                                              const double *, double *, double *, float *, cudaStream_t);
+template cudaError_t launch_visc_update<double>(const BoxDev &, const double *, const double *, int,
+                                               const double *, double *, double *, double *, cudaStream_t);
+
+}  // namespace nopcs

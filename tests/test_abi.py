@@ -1,0 +1,96 @@
+"""The C-ABI library loads, exports every symbol include/nopcs.h declares, and its
+host-side logic (argument checks, NOHAP operator tables) is right.  No GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nopcs.h")
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2203_00879_gb300 import build
+    build.build()
+    from paper_2203_00879_gb300 import nopcs
+    return nopcs
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(nopcs_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_the_four_entry_points():
+    names = declared_functions()
+    for n in ("nopcs_init", "nopcs_derivative", "nopcs_rk_step", "nopcs_diagnostics"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(N):
+    lib = ctypes.CDLL(N.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_has_same_names(N):
+    for n in declared_functions():
+        assert hasattr(N, n), n
+
+
+def test_init_rejects_bad_arguments_before_device_work(N):
+    import nopcs_synth as S
+    good = S.box_params((8, 8, 8))
+    cases = [dict(good, n=(4, 8, 8)), dict(good, sub_n=(2, 8, 8)), dict(good, gravity_axis=3),
+             dict(good, dt=0.0), dict(good, gamma=1.0), dict(good, filter_every=-1)]
+    for c in cases:
+        with pytest.raises(N.NopcsError) as ei:
+            N.nopcs_init([c])
+        assert ei.value.status == N.NOPCS_EINVAL
+    with pytest.raises(N.NopcsError):
+        N.nopcs_init([good], prec=7)
+    with pytest.raises(N.NopcsError) as ei:
+        N.nopcs_init([good], form=N.NOPCS_FORM_GEMM_BF16X3)
+    assert ei.value.status == N.NOPCS_EUNSUPPORTED
+
+
+def test_kernel_names(N):
+    names = [N.nopcs_kernel_name(k) for k in range(N.NOPCS_NUM_KERNELS)]
+    assert all(names) and len(set(names)) == len(names)
+    assert N.nopcs_kernel_name(N.NOPCS_NUM_KERNELS) is None
+
+
+@pytest.mark.parametrize("Nn,sub_n", [(5, 3), (7, 3), (48, 24), (50, 24), (101, 24), (257, 64), (129, 0)])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_operator_tables_match_oracle(N, Nn, sub_n, kind):
+    """The library's end rows (C = A^-1 B via transposed tridiagonal solves)
+    equal the oracle's dense C rows, and everything dropped is below 1e-16."""
+    starts, rows = N.nopcs_operator_rows(Nn, sub_n, kind=kind, alpha_f=0.135, thresh=1e-16)
+    assert list(starts) == list(oracle.partition(Nn, sub_n))
+    op = oracle.Op(Nn, kind=kind, sub_n=sub_n)
+    _, Cm = op.matrices()
+    for b in range(len(starts) - 1):
+        for which, i in ((0, starts[b]), (1, starts[b + 1] - 1)):
+            j0, c = rows[2 * b + which]
+            if which == 1 and starts[b + 1] - 1 == starts[b]:
+                continue
+            c = np.array(c)
+            assert np.max(np.abs(c - Cm[i, j0:j0 + len(c)])) < 1e-15
+            rest = np.ones(Nn, bool)
+            rest[j0:j0 + len(c)] = False
+            assert np.all(np.abs(Cm[i][rest]) < 1e-16)
+
+
+def test_fp32_tables_have_24_taps_each_side(N):
+    starts, rows = N.nopcs_operator_rows(1024, 64, kind=0, thresh=1e-8)
+    j0, c = rows[2 * 8]  # start of a sub-domain far from both walls
+    assert starts[8] == 512 and j0 == 512 - 24 and len(c) == 49
+    k = np.loadtxt(os.path.join(ROOT, "tests", "golden", "oucs3_equivalent_explicit_row.txt"))
+    ref = k[24:73, 1]
+    assert np.max(np.abs(np.array(c) - ref)) < 2e-16

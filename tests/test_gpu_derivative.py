@@ -1,0 +1,157 @@
+"""Parity of the CUDA NOHAP derivative (nopcs_derivative, through the C ABI)
+with the FP64 oracle.  FP64 path: <= 1e-12 of max |f'|; FP32 path: <= 1e-5."""
+import numpy as np
+import pytest
+
+import nopcs_synth as S
+import oracle
+from gpu_util import binding, field_rel, stream_ptr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def _ctx(N, n, sub_n):
+    p = S.box_params(n, sub_n=sub_n, perturb_amp=0.0)
+    return N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=stream_ptr()), p
+
+
+def _oracle(f, axis, h, sub_n, order):
+    d = oracle.deriv3d(f, axis, h, sub_n)
+    if order == 2:
+        d = oracle.deriv3d(d, axis, h, sub_n)
+    return d
+
+
+@pytest.mark.parametrize("n,sub_n", [((70, 45, 37), (24, 16, 0)), ((48, 48, 48), (24, 24, 24)),
+                                     ((5, 5, 5), (3, 3, 3)), ((7, 9, 11), (3, 4, 5)),
+                                     ((130, 66, 35), (64, 32, 8)), ((33, 200, 9), (0, 128, 3))])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_derivative_parity(n, sub_n, dtype):
+    import torch
+    N = binding()
+    ctx, p = _ctx(N, n, sub_n)
+    try:
+        f = S.sine_field(n, kmax=16, seed=7, noise=1e-3)
+        h = p["len"][0] / (n[0] - 1)
+        np_dt = np.float64 if dtype == 0 else np.float32
+        fd = to_dev(f, np_dt)
+        fin = fd.cpu().numpy().astype(np.float64)
+        out = torch.empty_like(fd)
+        for axis in range(3):
+            for order in (1, 2):
+                out.fill_(float("nan"))
+                N.nopcs_derivative(ctx, 0, axis, order, dtype, fd.data_ptr(), out.data_ptr(), stream_ptr())
+                torch.cuda.synchronize()
+                got = out.cpu().numpy().astype(np.float64)
+                ref = _oracle(fin, axis, h, sub_n[axis], order)
+                err = field_rel(got[None], ref[None])[0]
+                assert np.all(np.isfinite(got)), (axis, order)
+                assert err <= TOL[dtype], (axis, order, err)
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_derivative_exact_modified_wavenumber():
+    """Single sine mode along each axis: interior points follow the closed form."""
+    import torch
+    N = binding()
+    n = (200, 150, 130)
+    ctx, p = _ctx(N, n, (32, 32, 32))
+    a, b1, b2 = oracle.OUCS3[:3]
+    try:
+        h = p["len"][0] / (n[0] - 1)
+        kh = 0.9
+        for axis in range(3):
+            x = np.arange(n[axis]) * h
+            prof = np.sin(kh / h * x)
+            shape = [1, 1, 1]
+            shape[2 - axis] = n[axis]
+            f = np.broadcast_to(prof.reshape(shape), (n[2], n[1], n[0])).copy()
+            fd = to_dev(f)
+            out = torch.empty_like(fd)
+            N.nopcs_derivative(ctx, 0, axis, 1, 0, fd.data_ptr(), out.data_ptr(), stream_ptr())
+            torch.cuda.synchronize()
+            got = np.moveaxis(out.cpu().numpy(), 2 - axis, -1)[3, 4]
+            keq = (2 * b1 * np.sin(kh) + 2 * b2 * np.sin(2 * kh)) / (1 + 2 * a * np.cos(kh))
+            exact = keq / h * np.cos(kh / h * x)
+            inner = slice(60, n[axis] - 60)
+            assert np.max(np.abs(got[inner] - exact[inner])) < 1e-10 * keq / h
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_derivative_subdomain_independence_on_gpu():
+    """NOHAP: the GPU result does not depend on the sub-domain length."""
+    import torch
+    N = binding()
+    n = (160, 40, 40)
+    f = S.sine_field(n, kmax=8, seed=3, noise=0.0)
+    outs = []
+    for sn in (3, 8, 24, 64, 0):
+        ctx, p = _ctx(N, n, (sn, 8, 8))
+        try:
+            fd = to_dev(f)
+            out = torch.empty_like(fd)
+            N.nopcs_derivative(ctx, 0, 0, 1, 0, fd.data_ptr(), out.data_ptr(), stream_ptr())
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+        finally:
+            N.nopcs_destroy(ctx)
+    for o in outs[1:]:
+        assert field_rel(o[None], outs[-1][None])[0] < 1e-13
+
+
+def test_derivative_rejects_bad_arguments():
+    import torch
+    N = binding()
+    ctx, p = _ctx(N, (8, 8, 8), (0, 0, 0))
+    try:
+        f = torch.zeros(1024, dtype=torch.float64, device="cuda")
+        for args in ((0, 3, 1, 0), (0, 0, 3, 0), (0, 0, 1, 2), (1, 0, 1, 0)):
+            box, axis, order, dt = args
+            with pytest.raises(N.NopcsError):
+                N.nopcs_derivative(ctx, box, axis, order, dt, f.data_ptr(), f.data_ptr() + 4096, 0)
+        with pytest.raises(N.NopcsError):  # overlapping buffers
+            N.nopcs_derivative(ctx, 0, 0, 1, 0, f.data_ptr(), f.data_ptr(), 0)
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+@pytest.mark.parametrize("sub_n", [32, 64, 128])
+def test_derivative_512_sampled_lines(sub_n):
+    """Full-size 512^3 fields (the derivative benchmark), FP64 and FP32: sampled
+    lines of the GPU result against the oracle on the same lines."""
+    import torch
+    N = binding()
+    n = (512, 512, 512)
+    ctx, p = _ctx(N, n, (sub_n,) * 3)
+    rng = np.random.default_rng(sub_n)
+    try:
+        h = p["len"][0] / 511
+        px, py, pz = [torch.from_numpy(v).cuda() for v in S.sine_profiles(n, kmax=64, seed=7)]
+        g = torch.Generator(device="cuda").manual_seed(11)
+        f64 = (pz[:, None, None] + py[None, :, None] + px[None, None, :]).contiguous()
+        f64 += 1e-3 * torch.randn(f64.shape, generator=g, device="cuda", dtype=torch.float64)
+        for dtype, f in ((0, f64), (1, f64.float())):
+            out = torch.empty_like(f)
+            for axis in range(3):
+                N.nopcs_derivative(ctx, 0, axis, 1, dtype, f.data_ptr(), out.data_ptr(), stream_ptr())
+                torch.cuda.synchronize()
+                op = oracle.Op(512, sub_n=sub_n)
+                worst = 0.0
+                for _ in range(12):
+                    i, j = rng.integers(0, 512, 2)
+                    if axis == 0:
+                        lf, lo = f[i, j, :], out[i, j, :]
+                    elif axis == 1:
+                        lf, lo = f[i, :, j], out[i, :, j]
+                    else:
+                        lf, lo = f[:, i, j], out[:, i, j]
+                    ref = op.nopcs(lf.double().cpu().numpy(), 1.0 / h)
+                    got = lo.double().cpu().numpy()
+                    worst = max(worst, np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+                assert worst <= TOL[dtype], (dtype, axis, worst)
+    finally:
+        N.nopcs_destroy(ctx)

@@ -1,0 +1,204 @@
+"""Parity of the CUDA RK path (nopcs_init / nopcs_rhs / nopcs_rk_step /
+nopcs_filter / nopcs_diagnostics, through the C ABI) with the FP64 oracle.
+FP64 form: <= 1e-12 field-relative L-inf per conserved variable; mixed form:
+<= 1e-5 against the oracle's base-subtracted FP64 run."""
+import numpy as np
+import pytest
+
+import nopcs_synth as S
+import oracle
+from gpu_util import binding, field_rel, stream_ptr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(N, ctx, p, box=0):
+    import torch
+    Q = torch.empty((5, p["n"][2], p["n"][1], p["n"][0]), dtype=torch.float64, device="cuda")
+    N.nopcs_get_state(ctx, box, Q.data_ptr())
+    return Q.cpu().numpy()
+
+
+def _ctx(N, p, prec):
+    return N.nopcs_init([p], prec=prec, stream=stream_ptr())
+
+
+def test_initial_state_matches_oracle():
+    N = binding()
+    p = S.box_params((21, 18, 24), sub_n=(8, 8, 8), seed=5)
+    ctx = _ctx(N, p, N.NOPCS_FP64)
+    try:
+        Q = _state(N, ctx, p)
+        ref = oracle.Solver(p).initial_state()
+        assert np.all(field_rel(Q, ref) <= 1e-15)
+        # perturbation identical bit for bit (same generator, same counters)
+        assert np.array_equal(Q[1:4] != 0, ref[1:4] != 0)
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,bs", [(0, 0), (0, 1), (1, 1)])
+def test_rhs_matches_oracle(prec, bs):
+    """One right-hand-side evaluation on a perturbed state."""
+    import torch
+    N = binding()
+    p = S.box_params((26, 23, 30), sub_n=(8, 24, 12), base_subtract=bs, perturb_amp=1e-3, seed=9)
+    ctx = _ctx(N, p, prec)
+    try:
+        orc = oracle.Solver(p)
+        Q = orc.initial_state()
+        rng = np.random.default_rng(1)
+        Q[4] *= 1 + 1e-4 * rng.standard_normal(Q[4].shape)
+        Q[0] *= 1 + 1e-4 * rng.standard_normal(Q[0].shape)
+        ref = orc.rhs(Q)
+        ref[1:4][:, [0, -1]] = 0
+        ref[1:4][:, :, [0, -1]] = 0
+        ref[1:4][:, :, :, [0, -1]] = 0
+        r = torch.empty(Q.shape, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+        N.nopcs_rhs(ctx, 0, to_dev(Q).data_ptr(), r.data_ptr())
+        got = r.cpu().numpy().astype(np.float64)
+        err = field_rel(got, ref)
+        assert np.all(err <= (1e-12 if prec == 0 else 1e-4)), err
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,bs", [(0, 0), (0, 1), (1, 1)])
+def test_config0_50_steps(prec, bs):
+    """48^3 two-temperature box, sub-domains of 24, 50 RK4 steps at the paper's
+    time step, filter after step 50 (the small workload)."""
+    N = binding()
+    p = S.box_params((48, 48, 48), sub_n=(24, 24, 24), base_subtract=bs, seed=1)
+    ctx = _ctx(N, p, prec)
+    try:
+        N.nopcs_rk_step(ctx, 50)
+        Q = _state(N, ctx, p)
+        orc = oracle.Solver(p)
+        ref = orc.step(orc.initial_state(), 50)
+        err = field_rel(Q, ref)
+        tol = 1e-12 if prec == 0 else 1e-5
+        assert np.all(err <= tol), err
+        d = N.nopcs_diagnostics(ctx, 0)
+        assert d["step"] == 50 and d["nonfinite"] == 0
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_filter_matches_oracle():
+    N = binding()
+    for bs in (0, 1):
+        p = S.box_params((30, 27, 33), sub_n=(8, 16, 0), base_subtract=bs, perturb_amp=1e-3)
+        ctx = _ctx(N, p, N.NOPCS_FP64)
+        try:
+            orc = oracle.Solver(p)
+            N.nopcs_filter(ctx, 0)
+            Q = _state(N, ctx, p)
+            ref = orc.filter(orc.initial_state())
+            assert np.all(field_rel(Q, ref) <= 1e-13)
+        finally:
+            N.nopcs_destroy(ctx)
+
+
+def test_diagnostics_match_oracle():
+    N = binding()
+    p = S.box_params((20, 22, 26), sub_n=(8, 8, 8), perturb_amp=1e-3)
+    ctx = _ctx(N, p, N.NOPCS_FP64)
+    try:
+        N.nopcs_rk_step(ctx, 3)
+        Q = _state(N, ctx, p)
+        d = N.nopcs_diagnostics(ctx, 0)
+        r = oracle.Solver(p).diagnostics(Q)
+        for k in ("mass", "energy_total"):
+            assert abs(d[k] - r[k]) <= 1e-13 * abs(r[k])
+        for k in ("max_speed", "max_dp", "max_mach"):
+            assert abs(d[k] - r[k]) <= 1e-12 * abs(r[k])
+        assert np.allclose(d["momentum"], r["momentum"], rtol=1e-10, atol=1e-22)
+        d2 = N.nopcs_diagnostics(ctx, 0)
+        assert d2 == d  # fixed reduction order
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_deterministic_and_graph_equals_direct():
+    """Two contexts, one replaying the CUDA graph and one launching directly
+    with profiling on, give identical bits."""
+    N = binding()
+    p = S.box_params((40, 36, 44), sub_n=(16, 16, 16), filter_every=2)
+    outs = []
+    for prof in (0, 1):
+        ctx = _ctx(N, p, N.NOPCS_MIXED)
+        try:
+            N.nopcs_set_profiling(ctx, prof)
+            N.nopcs_rk_step(ctx, 5)
+            outs.append(_state(N, ctx, p))
+            if prof:
+                t = N.nopcs_profile_read(ctx)
+                assert t["sweep_x"][1] == 20 and t["filter"][1] == 2
+                assert all(v[0] > 0 for k, v in t.items() if k != "diagnostics")
+        finally:
+            N.nopcs_destroy(ctx)
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_isothermal_rest_state_large():
+    """128^3 isothermal quiescent box with gravity, mixed form: stays at rest."""
+    N = binding()
+    p = S.box_params((128, 128, 128), sub_n=(64, 64, 64), T_lower=1.0, perturb_amp=0.0)
+    ctx = _ctx(N, p, N.NOPCS_MIXED)
+    try:
+        N.nopcs_rk_step(ctx, 4)
+        d = N.nopcs_diagnostics(ctx, 0)
+        assert d["max_speed"] < 1e-12 and d["nonfinite"] == 0
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_mixed_128_against_oracle():
+    """128^3 config-0 physics, mixed form vs the FP64 base-subtracted oracle."""
+    N = binding()
+    p = S.box_params((128, 128, 128), sub_n=(64, 64, 64), base_subtract=1, seed=2, filter_every=5)
+    ctx = _ctx(N, p, N.NOPCS_MIXED)
+    try:
+        N.nopcs_rk_step(ctx, 10)
+        Q = _state(N, ctx, p)
+        orc = oracle.Solver(p)
+        ref = orc.step(orc.initial_state(), 10)
+        err = field_rel(Q, ref)
+        assert np.all(err <= 1e-5), err
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_batched_uneven_boxes():
+    """Several independent boxes of different shapes in one context advance
+    exactly as they do alone."""
+    N = binding()
+    boxes = [S.box_params((24, 20, 30), sub_n=(8, 8, 8), seed=3),
+             S.box_params((17, 33, 21), sub_n=(5, 16, 0), seed=4, T_lower=1.5)]
+    ctx = N.nopcs_init(boxes, prec=N.NOPCS_MIXED, stream=stream_ptr())
+    try:
+        N.nopcs_rk_step(ctx, 3)
+        both = [_state(N, ctx, p, b) for b, p in enumerate(boxes)]
+    finally:
+        N.nopcs_destroy(ctx)
+    for b, p in enumerate(boxes):
+        c1 = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=stream_ptr())
+        try:
+            N.nopcs_rk_step(c1, 3)
+            assert np.array_equal(_state(N, c1, p), both[b])
+        finally:
+            N.nopcs_destroy(c1)
+
+
+def test_set_get_state_host_roundtrip():
+    N = binding()
+    p = S.box_params((12, 13, 14))
+    ctx = _ctx(N, p, N.NOPCS_FP64)
+    try:
+        q = np.random.default_rng(0).standard_normal((5, 14, 13, 12)) + 2.0
+        N.nopcs_set_state(ctx, 0, q.ctypes.data)
+        back = np.empty_like(q)
+        N.nopcs_get_state(ctx, 0, back.ctypes.data)
+        assert np.array_equal(q, back)
+    finally:
+        N.nopcs_destroy(ctx)

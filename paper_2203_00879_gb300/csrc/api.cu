@@ -188,9 +188,10 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     hydrostatic(d, rh, ph);
     const int Ng = d.n[d.gravity_axis];
     const bool bs = d.base_subtract != 0;
-    // layout: rho_h, p_h, rho_b, p_b, E_b, H_b (double) then rho_b, p_b, H_b (float)
+    // layout: rho_h, p_h, rho_b, p_b, E_b, H_b (double) then
+    //         rho_b, p_b, H_b, T_b, 1/p_b, 1/rho_b (float)
     std::vector<double> t64(6 * (size_t)Ng, 0.0);
-    std::vector<float> t32(3 * (size_t)Ng, 0.0f);
+    std::vector<float> t32(6 * (size_t)Ng, 0.0f);
     for (int k = 0; k < Ng; ++k) {
         t64[k] = rh[k];
         t64[Ng + k] = ph[k];
@@ -203,6 +204,10 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
             t32[k] = (float)rh[k];
             t32[Ng + k] = (float)ph[k];
             t32[2 * Ng + k] = (float)(Eb + ph[k]);
+            const double zk = k * (d.len[d.gravity_axis] / (Ng - 1));
+            t32[3 * Ng + k] = (float)(zk < 0.5 * d.len[d.gravity_axis] ? d.T_lower : d.T_upper);
+            t32[4 * Ng + k] = (float)(1.0 / ph[k]);
+            t32[5 * Ng + k] = (float)(1.0 / rh[k]);
         }
     }
     const size_t b64 = t64.size() * 8, b32 = t32.size() * 4;
@@ -220,6 +225,9 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     x.rho_b32 = p32;
     x.p_b32 = p32 + Ng;
     x.H_b32 = p32 + 2 * Ng;
+    x.T_b32 = p32 + 3 * Ng;
+    x.ip_b32 = p32 + 4 * Ng;
+    x.ir_b32 = p32 + 5 * Ng;
 
     // state registers and scratch
     const size_t np = (size_t)x.np;
@@ -367,6 +375,7 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
+    if (e == cudaSuccess) e = init_visc_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         g_init_error = std::string("CUDA: ") + cudaGetErrorString(e);

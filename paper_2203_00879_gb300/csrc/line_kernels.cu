@@ -63,7 +63,8 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
-    constexpr int W = MODE == MODE_FILTER ? 3 : 2;  // right-hand-side half-width
+    constexpr int W = MODE == MODE_FILTER ? 3 : 2;     // right-hand-side half-width
+    constexpr int NEXP = MODE == MODE_FILTER ? 3 : 2;  // explicit rows at each wall
     const int LINES = a.lines, LP = a.lines + 1, RT = a.rt;
     const int nx = a.n[0], ny = a.n[1];
     const long long np = a.np;
@@ -87,46 +88,66 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     const int gsel = a.ga == AXIS ? 0 : (a.ga == (AXIS == 0 ? 1 : 0) ? 1 : 2);
 
     // ---- stage rows [tlo, thi] of nl lines -----------------------------------
+    // U items per thread per pass: all their global loads are issued before
+    // any is used, so each thread keeps several loads in flight.
+    constexpr int U = 4;
+    constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
     const int total = nrows * nl;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        int r, l;
-        if (AXIS == 0) {
-            r = q % nrows;
-            l = q / nrows;
-        } else {
-            l = q % nl;
-            r = q / nl;
+    const size_t fs = (size_t)RT * LP;
+    for (int q0 = threadIdx.x; q0 < total; q0 += U * blockDim.x) {
+        T v[U][NIN];
+        int rr[U], ll[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * blockDim.x;
+            rr[u] = -1;
+            if (q < total) {
+                int r, l;
+                if (AXIS == 0) {
+                    r = q % nrows;
+                    l = q / nrows;
+                } else {
+                    l = q % nl;
+                    r = q / nl;
+                }
+                rr[u] = r;
+                ll[u] = l;
+                const long long gi = gbase + (long long)(tlo + r) * srow + (long long)l * sa;
+#pragma unroll
+                for (int k = 0; k < NIN; ++k) v[u][k] = a.in[k * np + gi];
+            }
         }
-        const long long gi = gbase + (long long)(tlo + r) * srow + (long long)l * sa;
-        T *dst = sm + (size_t)r * LP + l;
-        if (MODE == MODE_FIELD) {
-            dst[0] = a.in[gi];
-        } else if (MODE == MODE_FLUX) {
-            const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
-            const T rho = a.b0[gk] + a.in[gi];
-            const T u = a.in[np + gi], v = a.in[2 * np + gi], w = a.in[3 * np + gi];
-            const T pp = a.in[4 * np + gi];
-            const T H = a.b1[gk] + a.in[5 * np + gi];
-            const T ud = AXIS == 0 ? u : (AXIS == 1 ? v : w);
-            const T m = rho * ud;
-            T f1 = m * u, f2 = m * v, f3 = m * w;
-            if (AXIS == 0) f1 += pp;
-            if (AXIS == 1) f2 += pp;
-            if (AXIS == 2) f3 += pp;
-            const size_t fs = (size_t)RT * LP;
-            dst[0] = m;
-            dst[fs] = f1;
-            dst[2 * fs] = f2;
-            dst[3 * fs] = f3;
-            dst[4 * fs] = H * ud;
-        } else {  // FILTER on Q - base
-            const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
-            const size_t fs = (size_t)RT * LP;
-            dst[0] = a.in[gi] - a.b0[gk];
-            dst[fs] = a.in[np + gi];
-            dst[2 * fs] = a.in[2 * np + gi];
-            dst[3 * fs] = a.in[3 * np + gi];
-            dst[4 * fs] = a.in[4 * np + gi] - a.b1[gk];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = rr[u], l = ll[u];
+            if (r < 0) continue;
+            T *dst = sm + (size_t)r * LP + l;
+            if constexpr (MODE == MODE_FIELD) {
+                dst[0] = v[u][0];
+            } else if constexpr (MODE == MODE_FLUX) {
+                const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
+                const T rho = a.b0[gk] + v[u][0];
+                const T uu = v[u][1], vv = v[u][2], ww = v[u][3], pp = v[u][4];
+                const T H = a.b1[gk] + v[u][5];
+                const T ud = AXIS == 0 ? uu : (AXIS == 1 ? vv : ww);
+                const T m = rho * ud;
+                T f1 = m * uu, f2 = m * vv, f3 = m * ww;
+                if (AXIS == 0) f1 += pp;
+                if (AXIS == 1) f2 += pp;
+                if (AXIS == 2) f3 += pp;
+                dst[0] = m;
+                dst[fs] = f1;
+                dst[2 * fs] = f2;
+                dst[3 * fs] = f3;
+                dst[4 * fs] = H * ud;
+            } else {  // FILTER on Q - base
+                const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
+                dst[0] = v[u][0] - a.b0[gk];
+                dst[fs] = v[u][1];
+                dst[2 * fs] = v[u][2];
+                dst[3 * fs] = v[u][3];
+                dst[4 * fs] = v[u][4] - a.b1[gk];
+            }
         }
     }
     __syncthreads();
@@ -138,7 +159,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
         T *col = sm + (size_t)fld * RT * LP + l;
         auto F = [&](int row) -> T { return col[(size_t)(row - tlo) * LP]; };
         const T *coef = coef_ptr<T>(op);
-        const int N = op.N, nexp = op.nexp;
+        const int N = op.N;
         // 1. end rows from the equivalent explicit scheme
         T gs = 0, ge = 0;
         {
@@ -154,8 +175,11 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             ge = acc;
         }
         // explicit wall-closure rows strictly inside the sub-domain
-        T exL[3] = {0, 0, 0}, exH[3] = {0, 0, 0};
-        for (int r = 0; r < nexp; ++r) {
+        T exL[NEXP], exH[NEXP];
+#pragma unroll
+        for (int r = 0; r < NEXP; ++r) {
+            exL[r] = 0;
+            exH[r] = 0;
             if (r > s && r < e) {
                 T acc = 0;
                 for (int j = 0; j < 5; ++j)
@@ -175,8 +199,8 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
         if (lo <= hi) {
             const int m = hi - lo + 1;
             const T al = (T)op.alpha;
-            const T gL = lo == s + 1 ? gs : exL[nexp - 1];
-            const T gR = hi == e - 1 ? ge : exH[nexp - 1];
+            const T gL = lo == s + 1 ? gs : exL[NEXP - 1];
+            const T gR = hi == e - 1 ? ge : exH[NEXP - 1];
             const T *cpp = cp_ptr<T>(op), *ivp = inv_ptr<T>(op);
             const T r0 = (T)op.rb[0], r1 = (T)op.rb[1], r2 = (T)op.rb[2], r3 = (T)op.rb[3];
             T win[2 * W + 1];
@@ -209,7 +233,8 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
         // explicit values into their rows
         col[(size_t)(s - tlo) * LP] = gs;
         if (rec[8] > 0) col[(size_t)(e - tlo) * LP] = ge;
-        for (int r = 0; r < nexp; ++r) {
+#pragma unroll
+        for (int r = 0; r < NEXP; ++r) {
             if (r > s && r < e) col[(size_t)(r - tlo) * LP] = exL[r];
             const int rh = N - 1 - r;
             if (rh > s && rh < e) col[(size_t)(rh - tlo) * LP] = exH[r];
@@ -220,35 +245,53 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     // ---- write the sub-domain's own rows ---------------------------------------
     const int nown = e - s + 1;
     const int tot2 = nown * nl;
-    for (int q = threadIdx.x; q < tot2; q += blockDim.x) {
-        int r, ll;
-        if (AXIS == 0) {
-            r = q % nown;
-            ll = q / nown;
-        } else {
-            ll = q % nl;
-            r = q / nl;
-        }
-        const long long gi = gbase + (long long)(s + r) * srow + (long long)ll * sa;
-        const T *src = sm + (size_t)(s - tlo + r) * LP + ll;
-        if (MODE == MODE_FIELD) {
-            a.out[gi] = src[0] * a.scale;
-        } else if (MODE == MODE_FLUX) {
-            const size_t fs = (size_t)RT * LP;
+    for (int q0 = threadIdx.x; q0 < tot2; q0 += U * blockDim.x) {
+        long long gi[U];
+        int rr[U], ll[U];
+        T old[U][5];
 #pragma unroll
-            for (int f = 0; f < 5; ++f) {
-                T v = -src[f * fs] * a.scale;
-                T *o = a.out + f * np + gi;
-                *o = a.first ? v : *o + v;
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * blockDim.x;
+            rr[u] = -1;
+            if (q < tot2) {
+                int r, l2;
+                if (AXIS == 0) {
+                    r = q % nown;
+                    l2 = q / nown;
+                } else {
+                    l2 = q % nl;
+                    r = q / nl;
+                }
+                rr[u] = r;
+                ll[u] = l2;
+                gi[u] = gbase + (long long)(s + r) * srow + (long long)l2 * sa;
+                if (MODE == MODE_FLUX && !a.first) {
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) old[u][f] = a.out[f * np + gi[u]];
+                }
             }
-        } else {
-            const int gk = gsel == 0 ? s + r : (gsel == 1 ? a0 + ll : cc);
-            const size_t fs = (size_t)RT * LP;
-            a.out[gi] = src[0] + a.b0[gk];
-            a.out[np + gi] = src[fs];
-            a.out[2 * np + gi] = src[2 * fs];
-            a.out[3 * np + gi] = src[3 * fs];
-            a.out[4 * np + gi] = src[4 * fs] + a.b1[gk];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = rr[u];
+            if (r < 0) continue;
+            const T *src = sm + (size_t)(s - tlo + r) * LP + ll[u];
+            if constexpr (MODE == MODE_FIELD) {
+                a.out[gi[u]] = src[0] * a.scale;
+            } else if constexpr (MODE == MODE_FLUX) {
+#pragma unroll
+                for (int f = 0; f < 5; ++f) {
+                    const T v = -src[f * fs] * a.scale;
+                    a.out[f * np + gi[u]] = a.first ? v : old[u][f] + v;
+                }
+            } else {
+                const int gk = gsel == 0 ? s + r : (gsel == 1 ? a0 + ll[u] : cc);
+                a.out[gi[u]] = src[0] + a.b0[gk];
+                a.out[np + gi[u]] = src[fs];
+                a.out[2 * np + gi[u]] = src[2 * fs];
+                a.out[3 * np + gi[u]] = src[3 * fs];
+                a.out[4 * np + gi[u]] = src[4 * fs] + a.b1[gk];
+            }
         }
     }
 }

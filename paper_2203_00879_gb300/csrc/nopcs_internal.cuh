@@ -75,6 +75,7 @@ struct BoxDev {
     double dt;
     const double *rho_b64, *p_b64, *H_b64, *E_b64;  // base tables along ga (zeros if plain)
     const float *rho_b32, *p_b32, *H_b32;
+    const float *T_b32, *ip_b32, *ir_b32;           // mixed form: T_b, 1/p_b, 1/rho_b
     const double *rho_h64, *p_h64;                  // hydrostatic profile (always)
 };
 
@@ -94,14 +95,17 @@ cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, co
 cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
                                const double *Qin, double *Qout, cudaStream_t st);
 
-// ---- launchers (rk_kernels.cu) ---------------------------------------------
-template <typename T>
-cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st);
+// ---- launchers (visc_kernel.cu) --------------------------------------------
+cudaError_t init_visc_kernels();
 // stage 1..4 of classical RK4, stage 0: R_total written to Rout (rhs only).
 template <typename T>
 cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage,
                                const double *Qn, double *acc, double *Qout, T *Rout,
                                cudaStream_t st);
+
+// ---- launchers (rk_kernels.cu) ---------------------------------------------
+template <typename T>
+cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st);
 cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, cudaStream_t st, int *launches);
 cudaError_t launch_initial_state(const BoxDev &bx, unsigned long long seed, double amp, double *Q,
                                  cudaStream_t st);

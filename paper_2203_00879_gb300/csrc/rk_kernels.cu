@@ -20,19 +20,6 @@ __device__ __forceinline__ void coords(const BoxDev &bx, long long p, int c[3])
     c[2] = (int)(q / bx.n[1]);
 }
 
-template <typename T>
-struct Base;
-template <>
-struct Base<double> {
-    static __device__ __forceinline__ const double *rho(const BoxDev &b) { return b.rho_b64; }
-    static __device__ __forceinline__ const double *p(const BoxDev &b) { return b.p_b64; }
-};
-template <>
-struct Base<float> {
-    static __device__ __forceinline__ const float *rho(const BoxDev &b) { return b.rho_b32; }
-    static __device__ __forceinline__ const float *p(const BoxDev &b) { return b.p_b32; }
-};
-
 // ---------------------------------------------------------------------------
 // Primitive recovery (Eqs. ge12, ge13, nondimensional): from the FP64 state to
 // W = (rho - rho_b, u, v, w, p - p_b, E + p - H_b) in the compute precision,
@@ -74,167 +61,6 @@ __global__ void prep_kernel(const BoxDev bx, const double *__restrict__ Q, T *__
             W[3 * np + p] = w;
             W[4 * np + p] = pd;
             W[5 * np + p] = Ed + pd;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Viscous terms (Sec. 4: second-order explicit), Eqs. ge19, bv1-bv3, ge20.
-// ---------------------------------------------------------------------------
-template <typename T>
-struct Visc {
-    const T *W;
-    long long np;
-    int n[3];
-    long long st[3];
-    T ih2[3];  // 1 / (2 h)
-    const T *rho_b, *p_b;
-    int ga;
-    T gm2, iRe, kq, S1, S, c0, c1;
-
-    __device__ __forceinline__ int gk(const int c[3]) const { return c[ga]; }
-    __device__ __forceinline__ T vel(int a, long long i) const { return W[(1 + a) * np + i]; }
-    __device__ __forceinline__ T temp(long long i, int kg) const
-    {
-        return gm2 * (p_b[kg] + W[4 * np + i]) / (rho_b[kg] + W[i]);
-    }
-    // derivative along axis a at node (coordinate ca, index i) of field f(i)
-    template <class Fn>
-    __device__ __forceinline__ T d1(int a, int ca, long long i, Fn f) const
-    {
-        const long long s = st[a];
-        if (ca == 0) return (T(-3) * f(i) + T(4) * f(i + s) - f(i + 2 * s)) * ih2[a];
-        if (ca == n[a] - 1) return (T(3) * f(i) - T(4) * f(i - s) + f(i - 2 * s)) * ih2[a];
-        return (f(i + s) - f(i - s)) * ih2[a];
-    }
-    // nodal viscous flux along axis d at node (c, i): tau_d0, tau_d1, tau_d2,
-    // u_a tau_da - q_d (q_d = 0 on a wall normal to d)
-    __device__ void flux(int d, const int c[3], long long i, T out[4]) const
-    {
-        const int kg0 = gk(c);
-        const T Tn = temp(i, kg0);
-        const T mu = Tn * sqrt(Tn) * S1 / (Tn + S);
-        const T mub = c0 * Tn + c1;
-        T gd[3];  // d u_a / d x_d
-        T ga_[3]; // d u_a / d x_a
-        T gx[3];  // d u_d / d x_a
-        for (int a = 0; a < 3; ++a) gd[a] = d1(d, c[d], i, [&](long long j) { return vel(a, j); });
-        for (int a = 0; a < 3; ++a) {
-            if (a == d) {
-                ga_[a] = gd[a];
-                gx[a] = gd[a];
-                continue;
-            }
-            ga_[a] = d1(a, c[a], i, [&](long long j) { return vel(a, j); });
-            gx[a] = d1(a, c[a], i, [&](long long j) { return vel(d, j); });
-        }
-        const T div = ga_[0] + ga_[1] + ga_[2];
-        T tau[3];
-        for (int a = 0; a < 3; ++a) {
-            if (a == d)
-                tau[a] = ((T(4) / T(3) * mu + mub) * gd[d] + (T(-2) / T(3) * mu + mub) * (div - gd[d])) * iRe;
-            else
-                tau[a] = mu * iRe * (gd[a] + gx[a]);
-        }
-        T q = T(0);
-        if (c[d] != 0 && c[d] != n[d] - 1) {
-            int cc[3] = {c[0], c[1], c[2]};
-            const T dT = d1(d, c[d], i, [&](long long j) {
-                // coordinate along the gravity axis of node j on the d-line
-                int off = (int)((j - i) / st[d]);
-                cc[d] = c[d] + off;
-                T t = temp(j, gk(cc));
-                cc[d] = c[d];
-                return t;
-            });
-            q = -mu * kq * dT;
-        }
-        out[0] = tau[0];
-        out[1] = tau[1];
-        out[2] = tau[2];
-        out[3] = vel(0, i) * tau[0] + vel(1, i) * tau[1] + vel(2, i) * tau[2] - q;
-    }
-};
-
-// R_total = R + div(viscous flux) + S, then the RK4 stage (stage 1..4) in FP64,
-// or (stage 0) R_total stored to Rout.
-template <typename T>
-__global__ void visc_update_kernel(const BoxDev bx, const Visc<T> V, const T *__restrict__ R, int stage,
-                                   const double *__restrict__ Qn, double *__restrict__ acc,
-                                   double *__restrict__ Qout, T *__restrict__ Rout)
-{
-    const long long np = bx.np;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
-         p += (long long)gridDim.x * blockDim.x) {
-        int c[3];
-        coords(bx, p, c);
-        T r[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) r[k] = R[k * np + p];
-        // divergence of the nodal viscous fluxes, same explicit operator
-        for (int d = 0; d < 3; ++d) {
-            const long long s = V.st[d];
-            T fa[4], fb[4], fc[4];
-            int cn[3] = {c[0], c[1], c[2]};
-            T dv[4];
-            if (c[d] == 0) {
-                V.flux(d, cn, p, fa);
-                cn[d] = 1;
-                V.flux(d, cn, p + s, fb);
-                cn[d] = 2;
-                V.flux(d, cn, p + 2 * s, fc);
-                for (int k = 0; k < 4; ++k) dv[k] = (T(-3) * fa[k] + T(4) * fb[k] - fc[k]) * V.ih2[d];
-            } else if (c[d] == bx.n[d] - 1) {
-                V.flux(d, cn, p, fa);
-                cn[d] = c[d] - 1;
-                V.flux(d, cn, p - s, fb);
-                cn[d] = c[d] - 2;
-                V.flux(d, cn, p - 2 * s, fc);
-                for (int k = 0; k < 4; ++k) dv[k] = (T(3) * fa[k] - T(4) * fb[k] + fc[k]) * V.ih2[d];
-            } else {
-                cn[d] = c[d] + 1;
-                V.flux(d, cn, p + s, fa);
-                cn[d] = c[d] - 1;
-                V.flux(d, cn, p - s, fb);
-                for (int k = 0; k < 4; ++k) dv[k] = (fa[k] - fb[k]) * V.ih2[d];
-            }
-            for (int k = 0; k < 4; ++k) r[1 + k] += dv[k];
-        }
-        // gravity source, Eq. ge8a: -(rho - rho_b) g in the momentum equation
-        // along the gravity axis, -rho u_g g in the energy equation
-        const int kg = c[bx.ga];
-        const T W0 = V.W[p];
-        const T rho = Base<T>::rho(bx)[kg] + W0;
-        const T ug = V.W[(1 + bx.ga) * np + p];
-        r[1 + bx.ga] -= W0 * (T)bx.g;
-        r[4] -= rho * ug * (T)bx.g;
-        // no-slip: momentum is held at zero on the walls
-        const bool wall = c[0] == 0 || c[0] == bx.n[0] - 1 || c[1] == 0 || c[1] == bx.n[1] - 1 || c[2] == 0 ||
-                          c[2] == bx.n[2] - 1;
-        if (wall) r[1] = r[2] = r[3] = T(0);
-        if (stage == 0) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) Rout[k * np + p] = r[k];
-            continue;
-        }
-        const double dt = bx.dt;
-        // classical RK4: acc accumulates Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
-        const double bw = (stage == 1 || stage == 4) ? dt / 6.0 : dt / 3.0;
-        const double cw = stage == 3 ? dt : 0.5 * dt;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const double rk = (double)r[k];
-            const long long o = k * np + p;
-            if (stage == 1) {
-                const double q = Qn[o];
-                acc[o] = q + bw * rk;
-                Qout[o] = q + cw * rk;
-            } else if (stage < 4) {
-                acc[o] = acc[o] + bw * rk;
-                Qout[o] = Qn[o] + cw * rk;
-            } else {
-                Qout[o] = acc[o] + bw * rk;
-            }
         }
     }
 }
@@ -442,35 +268,6 @@ __global__ void diag_final_kernel(const BoxDev bx, const double *partial, int nb
     for (int k = 0; k < DIAG_REC; ++k) out[k] = v[k];
 }
 
-template <typename T>
-Visc<T> make_visc(const BoxDev &bx, const T *W)
-{
-    Visc<T> V;
-    V.W = W;
-    V.np = bx.np;
-    for (int d = 0; d < 3; ++d) V.n[d] = bx.n[d];
-    V.st[0] = 1;
-    V.st[1] = bx.n[0];
-    V.st[2] = (long long)bx.n[0] * bx.n[1];
-    for (int d = 0; d < 3; ++d) V.ih2[d] = (T)(0.5 * bx.inv_h[d]);
-    if constexpr (sizeof(T) == 8) {
-        V.rho_b = (const T *)bx.rho_b64;
-        V.p_b = (const T *)bx.p_b64;
-    } else {
-        V.rho_b = (const T *)bx.rho_b32;
-        V.p_b = (const T *)bx.p_b32;
-    }
-    V.ga = bx.ga;
-    V.gm2 = (T)bx.gm2;
-    V.iRe = (T)(1.0 / bx.Re);
-    V.kq = (T)bx.kq;
-    V.S1 = (T)(1.0 + bx.suth_S);
-    V.S = (T)bx.suth_S;
-    V.c0 = (T)bx.mub_coef0;
-    V.c1 = (T)bx.mub_coef1;
-    return V;
-}
-
 int grid_for(long long work, int threads)
 {
     long long b = (work + threads - 1) / threads;
@@ -486,15 +283,6 @@ template <typename T>
 cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st)
 {
     prep_kernel<T><<<grid_for(bx.np, 256), 256, 0, st>>>(bx, Q, W);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const double *Qn,
-                               double *acc, double *Qout, T *Rout, cudaStream_t st)
-{
-    Visc<T> V = make_visc<T>(bx, W);
-    visc_update_kernel<T><<<grid_for(bx.np, 128), 128, 0, st>>>(bx, V, R, stage, Qn, acc, Qout, Rout);
     return cudaGetLastError();
 }
 
@@ -535,9 +323,4 @@ cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partia
 
 template cudaError_t launch_prep<float>(const BoxDev &, const double *, float *, cudaStream_t);
 template cudaError_t launch_prep<double>(const BoxDev &, const double *, double *, cudaStream_t);
-template cudaError_t launch_visc_update<float>(const BoxDev &, const float *, const float *, int,
-                                              const double *, double *, double *, float *, cudaStream_t);
-template cudaError_t launch_visc_update<double>(const BoxDev &, const double *, const double *, int,
-                                               const double *, double *, double *, double *, cudaStream_t);
-
 }  // namespace nopcs

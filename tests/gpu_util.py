@@ -31,3 +31,23 @@ def field_rel(a, b):
     d = np.abs(a - b).reshape(a.shape[0], -1).max(axis=1)
     s = np.abs(b).reshape(b.shape[0], -1).max(axis=1)
     return d / np.where(s == 0, 1.0, s)
+
+
+def state_err(Q, ref, p):
+    """Per-variable L-inf errors used as gates: rho and E relative to their
+    field maximum; momentum relative to max(rho) * max(c), c = sqrt(T)/M the
+    sound speed, the natural momentum scale of this compressible flow (the
+    flow's own momentum is 1e-4 of it or less, so its field-relative error
+    measures FP64 round-off of the O(1/(gamma M^2)) pressure terms, not
+    parity)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    gam, M = p["gamma"], p["M"]
+    rho = ref[0]
+    pr = (gam - 1) * (ref[4] - 0.5 * (ref[1] ** 2 + ref[2] ** 2 + ref[3] ** 2) / rho)
+    T = gam * M * M * pr / rho
+    mscale = np.max(np.abs(rho)) * np.sqrt(np.max(T)) / M
+    d = np.abs(Q - ref).reshape(5, -1).max(axis=1)
+    out = d / np.abs(ref).reshape(5, -1).max(axis=1)
+    out[1:4] = d[1:4] / mscale
+    return out

@@ -10,6 +10,11 @@ from gpu_util import binding, field_rel, stream_ptr, to_dev
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-12, 1: 1e-5}
+# order 2 applies the operator twice: the FP32 rounding of the first pass is
+# differentiated again, which amplifies it by up to the operator norm
+# max k_eq / h = 2.21 / h relative to the scale of the exact second derivative
+# of these noise-carrying fields (a factor of a few); allowed 5x the order-1 bound.
+TOL2 = {0: 1e-12, 1: 5e-5}
 
 
 def _ctx(N, n, sub_n):
@@ -48,7 +53,8 @@ def test_derivative_parity(n, sub_n, dtype):
                 ref = _oracle(fin, axis, h, sub_n[axis], order)
                 err = field_rel(got[None], ref[None])[0]
                 assert np.all(np.isfinite(got)), (axis, order)
-                assert err <= TOL[dtype], (axis, order, err)
+                assert err <= (TOL if order == 1 else TOL2)[dtype], (axis, order, err)
+                print("parity", n, sub_n, "dtype", dtype, "axis", axis, "order", order, "err %.3e" % err)
     finally:
         N.nopcs_destroy(ctx)
 

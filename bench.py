@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--fp64-n", type=int, default=1024, help="grid of the FP64-form comparison (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-n", type=int, default=64, help="oracle sample grid for the CPU baseline")
+    ap.add_argument("--cpu-n", type=int, default=128, help="oracle sample grid for the CPU baseline")
+    ap.add_argument("--cpu-steps", type=int, default=12, help="oracle sample steps for the CPU baseline")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -109,6 +110,22 @@ class Clocks:
         loaded = [s for s in sm if s > 0.5 * mx] or sm
         return {"sm_mhz": loaded[len(loaded) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(rows)}
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(points_per_rank, stages, steps, world, ms_max):
+    """Whole-job point-stage updates per second: every rank advances its own
+    box of `points_per_rank` points, the slowest rank sets the time."""
+    return world * float(points_per_rank) * stages * steps / (ms_max * 1e-3)
 
 
 def box(n, sub_n, **kw):
@@ -173,12 +190,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, dist, "cuda")
 
     stream = torch.cuda.current_stream()
     st = stream.cuda_stream
@@ -203,8 +216,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = N.nopcs_profile_read(ctx, reset=True)
     N.nopcs_set_profiling(ctx, False)
-    ms_max = max_over_ranks(ms)
-    value = world * npts * 4 * K / (ms_max * 1e-3)
+    ms_max = rank_max(ms)
+    value = job_rate(npts, 4, K, world, ms_max)
     launches_per_kind = {"prep": 1, "sweep_x": 1, "sweep_y": 1, "sweep_z": 1, "visc_rk_update": 1,
                          "wall_bc": 2, "filter": 3, "diagnostics": 2}
     gpu_launches = int(sum(v[1] * launches_per_kind.get(k, 1) for k, v in prof.items()))
@@ -254,7 +267,7 @@ def main():
             N.nopcs_rk_step(ctx, 1)
             N.nopcs_diagnostics(ctx, 0)
         barrier()
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = rank_max(time.perf_counter() - t0)
         e2e = {"value": world * npts * 4 * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 10 * 8, "pinned_host": pinned, "steps": args.e2e_steps}
         del host
@@ -279,7 +292,7 @@ def main():
         N.nopcs_rk_step(ctx, args.fp64_steps)
         e1.record(stream)
         barrier()
-        m64 = max_over_ranks(e0.elapsed_time(e1))
+        m64 = rank_max(e0.elapsed_time(e1))
         v64 = world * float(n64) ** 3 * 4 * args.fp64_steps / (m64 * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "grid": [n64] * 3, "steps": args.fp64_steps,
                 "ms_per_step": m64 / args.fp64_steps, "mixed_over_fp64": value / v64}
@@ -287,10 +300,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, dt, cores = run_cpu_oracle(args.cpu_n, 1)
+        rate, dt, cores = run_cpu_oracle(args.cpu_n, args.cpu_steps)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "FP64 CPU oracle, one RK4 step of a %d^3 box of the same physics (base-subtracted), "
-                         "%.1f s" % (args.cpu_n, dt)}
+               "sample": "FP64 CPU oracle, %d RK4 steps of a %d^3 box of the same physics (base-subtracted), "
+                         "%.1f s" % (args.cpu_steps, args.cpu_n, dt)}
 
     if rank == 0:
         line = {

@@ -149,6 +149,31 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
                               const void *f, void *df, void *stream);
 
 /*
+ * Allocation-free form of nopcs_derivative(order = 2).  The paper has no
+ * counterpart: this is a service for callers that cannot let the library
+ * allocate device memory during a call (their device memory belongs to their
+ * own pool allocator, or the implicit synchronisation of cudaMalloc/cudaFree
+ * is not acceptable in their loop), whereas nopcs_derivative allocates its
+ * order-2 scratch on first use.  Same arguments, result and arithmetic as
+ * nopcs_derivative with order 2; the intermediate first derivative lives in a
+ * fixed 16 MiB array in the library's device image, which every GPU that loads
+ * the library holds until the process exits.  Limits and behaviour:
+ *   - fields of at most 2^21 FP64 or 2^22 FP32 points; larger ones return
+ *     NOPCS_EINVAL with a message (nothing is enqueued);
+ *   - the first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture;
+ *   - all calls share the one array, so two calls whose work overlaps on the
+ *     GPU (different streams, no ordering between them) race on it; the array
+ *     keeps the last call's contents, and each call overwrites every element
+ *     it reads before reading it;
+ *   - no cudaMalloc, cudaFree or other allocating routine is called.
+ * Errors: EINVAL (as nopcs_derivative, plus the size limit), ECUDA.
+ */
+nopcs_status nopcs_derivative2_noalloc(nopcs_ctx *ctx, int box, int axis, int dtype, const void *f, void *df,
+                                       void *stream);
+
+/*
  * Advance every box by `nsteps` classical RK4 steps of dt (Sec. 4), applying
  * the no-slip adiabatic wall conditions after every stage and the filter after
  * every filter_every steps (counted per box from its initial state).  Enqueued

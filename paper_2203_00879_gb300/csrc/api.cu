@@ -352,6 +352,27 @@ nopcs_status check_box(nopcs_ctx *ctx, int box)
 
 }  // namespace
 
+namespace nopcs {
+
+nopcs_status ctx_derivative_operator(nopcs_ctx *ctx, int box, int axis, int dtype, const LineOpDev **op,
+                                     const int **n, long long *np, double *scale)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (axis < 0 || axis > 2) return fail(ctx, NOPCS_EINVAL, "axis must be 0, 1 or 2");
+    if (dtype != 0 && dtype != 1) return fail(ctx, NOPCS_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
+    BoxRes &b = ctx->boxes[box];
+    *op = dtype == 0 ? &b.dop64[axis].dev : &b.dop32[axis].dev;
+    *n = b.dev.n;
+    *np = b.dev.np;
+    *scale = b.dev.inv_h[axis];
+    return NOPCS_OK;
+}
+
+nopcs_status ctx_error(nopcs_ctx *ctx, nopcs_status s, const char *msg) { return fail(ctx, s, msg); }
+
+}  // namespace nopcs
+
 // ============================================================================
 extern "C" {
 

@@ -114,4 +114,12 @@ cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partia
                                double *out, cudaStream_t st);
 int diag_blocks(long long np);
 
+// ---- context access for entry points outside api.cu ------------------------
+// Operator and geometry of box `box` for a derivative along `axis` in `dtype`
+// (0 f64, 1 f32); validates the box index.  Returns NOPCS_OK or sets the
+// context's error message.
+nopcs_status ctx_derivative_operator(nopcs_ctx *ctx, int box, int axis, int dtype, const LineOpDev **op,
+                                     const int **n, long long *np, double *scale);
+nopcs_status ctx_error(nopcs_ctx *ctx, nopcs_status s, const char *msg);
+
 }  // namespace nopcs

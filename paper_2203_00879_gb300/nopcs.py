@@ -56,6 +56,7 @@ _L.nopcs_set_state.argtypes = [_vp, _i, _vp]
 _L.nopcs_get_state.argtypes = [_vp, _i, _vp]
 _L.nopcs_reset_state.argtypes = [_vp, _i]
 _L.nopcs_derivative.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp, _vp]
+_L.nopcs_derivative2_noalloc.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp]
 _L.nopcs_rk_step.argtypes = [_vp, _i]
 _L.nopcs_rhs.argtypes = [_vp, _i, _vp, _vp]
 _L.nopcs_filter.argtypes = [_vp, _i]
@@ -68,6 +69,7 @@ _L.nopcs_kernel_name.restype = C.c_char_p
 _L.nopcs_operator_rows.argtypes = [_i, _i, _i, _d, _d, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
                                    C.POINTER(_i), C.POINTER(_d), _i]
 for _name in ("nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
+              "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
               "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows"):
     getattr(_L, _name).restype = _i
@@ -128,6 +130,13 @@ def nopcs_reset_state(ctx, box: int) -> None:
 def nopcs_derivative(ctx, box: int, axis: int, order: int, dtype: int, f_ptr: int, df_ptr: int,
                      stream: int = 0) -> None:
     _check(ctx, _L.nopcs_derivative(ctx, box, axis, order, dtype, f_ptr, df_ptr, _vp(stream or None)))
+
+
+def nopcs_derivative2_noalloc(ctx, box: int, axis: int, dtype: int, f_ptr: int, df_ptr: int,
+                              stream: int = 0) -> None:
+    """Second derivative without any device allocation in the call (fixed
+    16 MiB library scratch; see include/nopcs.h for the limits)."""
+    _check(ctx, _L.nopcs_derivative2_noalloc(ctx, box, axis, dtype, f_ptr, df_ptr, _vp(stream or None)))
 
 
 def nopcs_rk_step(ctx, nsteps: int) -> None:

@@ -33,7 +33,8 @@ ALG_BYTES_MIXED = {
     "sweep_x": 24 + 20,                # read W, write R (5 f32)
     "sweep_y": 24 + 40,                # read W, read+write R
     "sweep_z": 24 + 40,
-    "visc_rk_update": (164 + 204 + 204 + 124) / 4.0,  # W, R, FP64 registers; stage average
+    # stage average of W + R + Dn (+ K) in, K + W' out; stage 4 also Q_n in/out and Dn out
+    "visc_rk_update": (108 + 128 + 128 + 188) / 4.0,
     "filter": 3 * 80,                  # three sweeps, each read+write Q
 }
 ALG_BYTES_FP64 = {

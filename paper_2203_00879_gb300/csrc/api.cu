@@ -19,11 +19,18 @@ enum { K_PREP = 0, K_SX, K_SY, K_SZ, K_VISC, K_BC, K_FILTER, K_DIAG };
 
 thread_local std::string g_init_error;
 
+// Device registers of a box.
+//   FP64 form: Q = Qn, Qs, acc (15 FP64 fields); W (6 FP64); R (5 FP64).
+//   Mixed form: Q = Qn (5 FP64 fields); W = slab of two FP32 primitive sets
+//     W0, W1 (12 fields); R = slab of R, K, Dn (15 FP32 fields).  Between
+//     steps W0 and Dn hold the primitives and the base deviation of Qn, and
+//     the filter borrows both slabs as FP64 temporaries.
 struct BoxRes {
     nopcs_box_desc d{};
     BoxDev dev{};
     LineOpBuf dop64[3], dop32[3], fop[3];
-    double *Q = nullptr;  // 3 registers of 5 fields: Qn, Qs, acc
+    bool mixed = false;
+    double *Q = nullptr;
     void *W = nullptr, *R = nullptr;
     void *base = nullptr;
     double *partial = nullptr, *diag_out = nullptr;
@@ -33,6 +40,10 @@ struct BoxRes {
     double *Qn() const { return Q; }
     double *Qs() const { return Q + 5 * dev.np; }
     double *acc() const { return Q + 10 * dev.np; }
+    float *Wm(int k) const { return (float *)W + (size_t)k * 6 * dev.np; }
+    float *Rm() const { return (float *)R; }
+    float *Km() const { return (float *)R + 5 * dev.np; }
+    float *Dn() const { return (float *)R + 10 * dev.np; }
 };
 
 struct ProfPair {
@@ -149,6 +160,13 @@ void free_box(BoxRes &b)
     b.partial = b.diag_out = nullptr;
 }
 
+// mixed form: primitives W0 and base deviation Dn of the FP64 state Qn
+cudaError_t refresh_mixed(BoxRes &b, cudaStream_t st)
+{
+    if (!b.mixed) return cudaSuccess;
+    return launch_prep<float>(b.dev, b.Qn(), b.Wm(0), b.Dn(), st);
+}
+
 nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
 {
     const nopcs_box_desc &d = b.d;
@@ -231,17 +249,18 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
 
     // state registers and scratch
     const size_t np = (size_t)x.np;
-    cudaError_t e = cudaMalloc(&b.Q, 15 * np * sizeof(double));
+    b.mixed = ctx->prec == NOPCS_MIXED;
+    cudaError_t e = cudaMalloc(&b.Q, (b.mixed ? 5 : 15) * np * sizeof(double));
     if (e != cudaSuccess) {
         b.Q = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "state registers");
     }
-    e = cudaMalloc(&b.W, 6 * np * esize(ctx));
+    e = cudaMalloc(&b.W, (b.mixed ? 12 : 6) * np * esize(ctx));
     if (e != cudaSuccess) {
         b.W = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "primitive buffer");
     }
-    e = cudaMalloc(&b.R, 5 * np * esize(ctx));
+    e = cudaMalloc(&b.R, (b.mixed ? 15 : 5) * np * esize(ctx));
     if (e != cudaSuccess) {
         b.R = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "right-hand-side buffer");
@@ -250,6 +269,7 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     CK(cudaMalloc(&b.partial, ((size_t)b.nblk_diag * 10 + 16) * sizeof(double)), "diagnostics scratch");
     b.diag_out = b.partial + (size_t)b.nblk_diag * 10;
     CK(launch_initial_state(x, d.seed, d.perturb_amp, b.Qn(), ctx->stream), "initial state");
+    CK(refresh_mixed(b, ctx->stream), "initial state");
     b.step = 0;
     return NOPCS_OK;
 }
@@ -290,34 +310,83 @@ struct Timed {
 };
 
 // ---- the RK stage sequence --------------------------------------------------
+// Sweeps x, y, z accumulate the convective right-hand side of W into R, then
+// the fused viscous/source/RK kernel finishes the stage.
 template <typename T>
-cudaError_t enqueue_stage(nopcs_ctx *ctx, BoxRes &b, int stage, const double *Qin, T *Rout, cudaStream_t st)
+cudaError_t enqueue_rhs_sweeps(nopcs_ctx *ctx, BoxRes &b, const T *W, T *R, cudaStream_t st)
+{
+    const bool f32 = sizeof(T) == 4;
+    for (int a = 0; a < 3; ++a) {
+        Timed t(ctx, st, K_SX + a);
+        cudaError_t e = launch_line_flux<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, b.dev, W, R, a == 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// FP64 form: stage s of classical RK4 from the FP64 stage state Qin
+cudaError_t enqueue_stage_fp64(nopcs_ctx *ctx, BoxRes &b, int stage, const double *Qin, double *Rout,
+                               cudaStream_t st)
 {
     const BoxDev &x = b.dev;
-    T *W = (T *)b.W, *R = (T *)b.R;
-    const bool f32 = sizeof(T) == 4;
+    double *W = (double *)b.W, *R = (double *)b.R;
     cudaError_t e;
     {
         Timed t(ctx, st, K_PREP);
-        e = launch_prep<T>(x, Qin, W, st);
+        e = launch_prep<double>(x, Qin, W, nullptr, st);
     }
     if (e != cudaSuccess) return e;
-    for (int a = 0; a < 3; ++a) {
-        Timed t(ctx, st, K_SX + a);
-        e = launch_line_flux<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, x, W, R, a == 0, st);
-        if (e != cudaSuccess) return e;
-    }
-    double *Qout = stage == 4 ? b.Qn() : b.Qs();
+    if ((e = enqueue_rhs_sweeps<double>(ctx, b, W, R, st)) != cudaSuccess) return e;
+    StageRegs<double> g;
+    g.Qn = b.Qn();
+    g.acc = b.acc();
+    g.Qout = stage == 4 ? b.Qn() : b.Qs();
+    g.Rout = Rout;
     {
         Timed t(ctx, st, K_VISC);
-        e = launch_visc_update<T>(x, W, R, stage, b.Qn(), b.acc(), Qout, Rout, st);
+        e = launch_visc_update<double>(x, W, R, stage, g, st);
     }
     if (e != cudaSuccess || stage == 0) return e;
+    Timed t(ctx, st, K_BC);
+    return launch_wall_bc(x, g.Qout, nullptr, nullptr, nullptr, st);
+}
+
+// Mixed form: stage s reads the primitives W_in (W0 for stages 1 and 3, W1
+// for 2 and 4) and writes those of the next stage state to the other set, so
+// every step starts and ends on W0.
+cudaError_t enqueue_stage_mixed(nopcs_ctx *ctx, BoxRes &b, int stage, cudaStream_t st)
+{
+    const BoxDev &x = b.dev;
+    float *Win = b.Wm((stage - 1) & 1), *Wout = b.Wm(stage & 1);
+    cudaError_t e = enqueue_rhs_sweeps<float>(ctx, b, Win, b.Rm(), st);
+    if (e != cudaSuccess) return e;
+    StageRegs<float> g;
+    g.Qn = b.Qn();
+    g.Kacc = b.Km();
+    g.Dn = b.Dn();
+    g.Wn = Wout;
     {
-        Timed t(ctx, st, K_BC);
-        e = launch_wall_bc(x, Qout, st, nullptr);
+        Timed t(ctx, st, K_VISC);
+        e = launch_visc_update<float>(x, Win, b.Rm(), stage, g, st);
     }
-    return e;
+    if (e != cudaSuccess) return e;
+    Timed t(ctx, st, K_BC);
+    if (stage < 4) return launch_wall_bc(x, nullptr, nullptr, nullptr, Wout, st);
+    return launch_wall_bc(x, b.Qn(), b.Dn(), Wout, nullptr, st);
+}
+
+// right-hand side of an FP64 state q into r (stage 0), for tests
+cudaError_t enqueue_rhs_only(nopcs_ctx *ctx, BoxRes &b, const double *q, void *r, cudaStream_t st)
+{
+    if (!b.mixed) return enqueue_stage_fp64(ctx, b, 0, q, (double *)r, st);
+    // W1 is free between steps
+    float *W = b.Wm(1);
+    cudaError_t e = launch_prep<float>(b.dev, q, W, nullptr, st);
+    if (e != cudaSuccess) return e;
+    if ((e = enqueue_rhs_sweeps<float>(ctx, b, W, b.Rm(), st)) != cudaSuccess) return e;
+    StageRegs<float> g;
+    g.Rout = (float *)r;
+    return launch_visc_update<float>(b.dev, W, b.Rm(), 0, g, st);
 }
 
 cudaError_t enqueue_filter(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
@@ -325,19 +394,23 @@ cudaError_t enqueue_filter(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
     Timed t(ctx, st, K_FILTER);
     const BoxDev &x = b.dev;
     const int bs = b.d.base_subtract;
-    cudaError_t e = launch_line_filter(b.fop[0].dev, 0, x, bs, b.Qn(), b.acc(), st);
+    // two FP64 temporaries: acc and Qs (FP64 form), the two FP32 slabs (mixed form)
+    double *t1 = b.mixed ? (double *)b.W : b.acc();
+    double *t2 = b.mixed ? (double *)b.R : b.Qs();
+    cudaError_t e = launch_line_filter(b.fop[0].dev, 0, x, bs, b.Qn(), t1, st);
     if (e != cudaSuccess) return e;
-    e = launch_line_filter(b.fop[1].dev, 1, x, bs, b.acc(), b.Qs(), st);
+    e = launch_line_filter(b.fop[1].dev, 1, x, bs, t1, t2, st);
     if (e != cudaSuccess) return e;
-    return launch_line_filter(b.fop[2].dev, 2, x, bs, b.Qs(), b.Qn(), st);
+    e = launch_line_filter(b.fop[2].dev, 2, x, bs, t2, b.Qn(), st);
+    if (e != cudaSuccess) return e;
+    return refresh_mixed(b, st);
 }
 
 cudaError_t enqueue_step(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
 {
     for (int s = 1; s <= 4; ++s) {
-        const double *Qin = s == 1 ? b.Qn() : b.Qs();
-        cudaError_t e = ctx->prec == NOPCS_MIXED ? enqueue_stage<float>(ctx, b, s, Qin, nullptr, st)
-                                                 : enqueue_stage<double>(ctx, b, s, Qin, nullptr, st);
+        cudaError_t e = b.mixed ? enqueue_stage_mixed(ctx, b, s, st)
+                                : enqueue_stage_fp64(ctx, b, s, s == 1 ? b.Qn() : b.Qs(), nullptr, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -452,6 +525,7 @@ nopcs_status nopcs_set_state(nopcs_ctx *ctx, int box, const double *q)
     BoxRes &b = ctx->boxes[box];
     CK(cudaMemcpyAsync(b.Qn(), q, 5 * (size_t)b.dev.np * sizeof(double), cudaMemcpyDefault, ctx->stream),
        "set_state");
+    CK(refresh_mixed(b, ctx->stream), "set_state");
     CK(cudaStreamSynchronize(ctx->stream), "set_state");
     return NOPCS_OK;
 }
@@ -474,6 +548,7 @@ nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box)
     if (s != NOPCS_OK) return s;
     BoxRes &b = ctx->boxes[box];
     CK(launch_initial_state(b.dev, b.d.seed, b.d.perturb_amp, b.Qn(), ctx->stream), "reset_state");
+    CK(refresh_mixed(b, ctx->stream), "reset_state");
     b.step = 0;
     return NOPCS_OK;
 }
@@ -567,8 +642,7 @@ nopcs_status nopcs_rhs(nopcs_ctx *ctx, int box, const double *q, void *r)
     if (s != NOPCS_OK) return s;
     if (!q || !r) return fail(ctx, NOPCS_EINVAL, "null pointer");
     BoxRes &b = ctx->boxes[box];
-    cudaError_t e = ctx->prec == NOPCS_MIXED ? enqueue_stage<float>(ctx, b, 0, q, (float *)r, ctx->stream)
-                                             : enqueue_stage<double>(ctx, b, 0, q, (double *)r, ctx->stream);
+    cudaError_t e = enqueue_rhs_only(ctx, b, q, r, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs");
     CK(cudaStreamSynchronize(ctx->stream), "rhs");
     return NOPCS_OK;

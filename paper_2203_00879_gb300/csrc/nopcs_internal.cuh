@@ -97,16 +97,32 @@ cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, 
 
 // ---- launchers (visc_kernel.cu) --------------------------------------------
 cudaError_t init_visc_kernels();
-// stage 1..4 of classical RK4, stage 0: R_total written to Rout (rhs only).
+// Registers of one RK stage.
+//   FP64 form: acc accumulates Q_n + dt sum b_s k_s, Qout receives the next
+//     stage state (stage 4: the new Q_n).
+//   Mixed form: Kacc accumulates k1 + 2 k2 + 2 k3 (FP32), Dn holds the FP32
+//     deviation of Q_n from the hydrostatic base, Wn receives the primitives of
+//     the next stage state; stage 4 adds dt/6 (K + k4) to Q_n in FP64 and
+//     refreshes Dn.
+// stage 0: the right-hand side is written to Rout and nothing else.
 template <typename T>
-cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage,
-                               const double *Qn, double *acc, double *Qout, T *Rout,
+struct StageRegs {
+    double *Qn = nullptr, *acc = nullptr, *Qout = nullptr;
+    float *Kacc = nullptr, *Dn = nullptr;
+    T *Wn = nullptr;
+    T *Rout = nullptr;
+};
+template <typename T>
+cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
                                cudaStream_t st);
 
 // ---- launchers (rk_kernels.cu) ---------------------------------------------
+// W from the FP64 state; Dn (mixed form, optional): deviation from the base.
 template <typename T>
-cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st);
-cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, cudaStream_t st, int *launches);
+cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, float *Dn, cudaStream_t st);
+// Wall conditions.  Q != nullptr: on the FP64 state (refreshing Dn and Wf at
+// the wall nodes when given); Q == nullptr: on the FP32 stage primitives Ww.
+cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, float *Dn, float *Wf, float *Ww, cudaStream_t st);
 cudaError_t launch_initial_state(const BoxDev &bx, unsigned long long seed, double amp, double *Q,
                                  cudaStream_t st);
 // partial: nblk * 10 doubles scratch; out: 10 doubles (device)

@@ -29,7 +29,8 @@ __device__ __forceinline__ void coords(const BoxDev &bx, long long p, int c[3])
 // p - p_b = (gamma - 1)(E - E_b - rho |V|^2 / 2) and H - H_b = (E - E_b) + (p - p_b).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void prep_kernel(const BoxDev bx, const double *__restrict__ Q, T *__restrict__ W)
+__global__ void prep_kernel(const BoxDev bx, const double *__restrict__ Q, T *__restrict__ W,
+                            float *__restrict__ Dn)
 {
     const long long np = bx.np;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
@@ -61,6 +62,13 @@ __global__ void prep_kernel(const BoxDev bx, const double *__restrict__ Q, T *__
             W[3 * np + p] = w;
             W[4 * np + p] = pd;
             W[5 * np + p] = Ed + pd;
+            if (Dn) {  // deviation of the state from the hydrostatic base (mixed form)
+                Dn[p] = rd;
+                Dn[np + p] = (float)mx;
+                Dn[2 * np + p] = (float)my;
+                Dn[3 * np + p] = (float)mz;
+                Dn[4 * np + p] = Ed;
+            }
         }
     }
 }
@@ -79,7 +87,7 @@ __device__ __forceinline__ double temp_q(const BoxDev &bx, const double *Q, long
     return bx.gm2 * (bx.gamma - 1.0) * (Q[4 * np + i] - ke) / r;
 }
 
-__device__ void set_wall_node(const BoxDev &bx, double *Q, const int c[3])
+__device__ void set_wall_node(const BoxDev &bx, double *Q, const int c[3], float *Dn, float *Wf)
 {
     const long long st[3] = {1, bx.n[0], (long long)bx.n[0] * bx.n[1]};
     const long long i = c[0] + st[1] * c[1] + st[2] * c[2];
@@ -100,10 +108,74 @@ __device__ void set_wall_node(const BoxDev &bx, double *Q, const int c[3])
     const long long np = bx.np;
     Q[np + i] = Q[2 * np + i] = Q[3 * np + i] = 0.0;
     Q[4 * np + i] = Q[i] * Tw * bx.cE;
+    if (Dn) {
+        const int kg = c[bx.ga];
+        const float rd = (float)(Q[i] - bx.rho_b64[kg]);
+        const float Ed = (float)(Q[4 * np + i] - bx.E_b64[kg]);
+        const float pd = (float)(bx.gamma - 1.0) * Ed;
+        Dn[i] = rd;
+        Dn[np + i] = Dn[2 * np + i] = Dn[3 * np + i] = 0.0f;
+        Dn[4 * np + i] = Ed;
+        Wf[i] = rd;
+        Wf[np + i] = Wf[2 * np + i] = Wf[3 * np + i] = 0.0f;
+        Wf[4 * np + i] = pd;
+        Wf[5 * np + i] = Ed + pd;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same wall conditions on an FP32 stage state held as W (mixed form):
+// T = T_b + T' with T' = T_b (p'/p_b - rho'/rho_b) / (1 + rho'/rho_b), the
+// extrapolated wall temperature kept as its difference dT from T_b at the
+// node, and E_w - E_b = cE (rho' T_w + rho_b dT) (E_b = cE rho_b T_b).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float temp_dev_w(const BoxDev &bx, const float *W, long long i, int kg)
+{
+    const long long np = bx.np;
+    const float rr = W[i] * bx.ir_b32[kg];
+    return bx.T_b32[kg] * (W[4 * np + i] * bx.ip_b32[kg] - rr) / (1.0f + rr);
+}
+
+__device__ void set_wall_node_w(const BoxDev &bx, float *W, const int c[3])
+{
+    const long long st[3] = {1, bx.n[0], (long long)bx.n[0] * bx.n[1]};
+    const long long i = c[0] + st[1] * c[1] + st[2] * c[2];
+    const int kg = c[bx.ga];
+    const float TbP = bx.T_b32[kg];
+    float dT = 0.0f;
+    int nw = 0;
+    for (int d = 0; d < 3; ++d) {
+        int sg;
+        if (c[d] == 0)
+            sg = 1;
+        else if (c[d] == bx.n[d] - 1)
+            sg = -1;
+        else
+            continue;
+        const long long s = sg * st[d];
+        int k1 = kg, k2 = kg;
+        if (d == bx.ga) {
+            k1 = kg + sg;
+            k2 = kg + 2 * sg;
+        }
+        const float d1 = (bx.T_b32[k1] - TbP) + temp_dev_w(bx, W, i + s, k1);
+        const float d2 = (bx.T_b32[k2] - TbP) + temp_dev_w(bx, W, i + 2 * s, k2);
+        dT += (4.0f * d1 - d2) * (1.0f / 3.0f);
+        ++nw;
+    }
+    dT /= (float)nw;
+    const long long np = bx.np;
+    const float rd = W[i];
+    const float Ed = (float)bx.cE * (rd * (TbP + dT) + bx.rho_b32[kg] * dT);
+    const float pd = (float)(bx.gamma - 1.0) * Ed;
+    W[np + i] = W[2 * np + i] = W[3 * np + i] = 0.0f;
+    W[4 * np + i] = pd;
+    W[5 * np + i] = Ed + pd;
 }
 
 // face nodes: exactly one wall coordinate
-__global__ void wall_face_kernel(const BoxDev bx, double *Q)
+// Q != nullptr: FP64 state (and Dn, Wf refreshed when given); else Ww: FP32 W
+__global__ void wall_face_kernel(const BoxDev bx, double *Q, float *Dn, float *Wf, float *Ww)
 {
     const int nx = bx.n[0], ny = bx.n[1], nz = bx.n[2];
     const long long fx = (long long)(ny - 2) * (nz - 2), fy = (long long)(nx - 2) * (nz - 2),
@@ -133,12 +205,15 @@ __global__ void wall_face_kernel(const BoxDev bx, double *Q)
             c[0] = 1 + (int)(q % (nx - 2));
             c[1] = 1 + (int)(q / (nx - 2));
         }
-        set_wall_node(bx, Q, c);
+        if (Q)
+            set_wall_node(bx, Q, c, Dn, Wf);
+        else
+            set_wall_node_w(bx, Ww, c);
     }
 }
 
 // edges (two wall coordinates), then corners; one block
-__global__ void wall_edge_corner_kernel(const BoxDev bx, double *Q)
+__global__ void wall_edge_corner_kernel(const BoxDev bx, double *Q, float *Dn, float *Wf, float *Ww)
 {
     const int n[3] = {bx.n[0], bx.n[1], bx.n[2]};
     // edge along axis a: the other two axes at 0 or n-1 (4 combinations)
@@ -159,13 +234,19 @@ __global__ void wall_edge_corner_kernel(const BoxDev bx, double *Q)
         c[a] = along;
         c[b1] = (combo & 1) ? n[b1] - 1 : 0;
         c[b2] = (combo & 2) ? n[b2] - 1 : 0;
-        set_wall_node(bx, Q, c);
+        if (Q)
+            set_wall_node(bx, Q, c, Dn, Wf);
+        else
+            set_wall_node_w(bx, Ww, c);
     }
     __syncthreads();
     if (threadIdx.x < 8) {
         int c[3];
         for (int d = 0; d < 3; ++d) c[d] = (threadIdx.x >> d) & 1 ? n[d] - 1 : 0;
-        set_wall_node(bx, Q, c);
+        if (Q)
+            set_wall_node(bx, Q, c, Dn, Wf);
+        else
+            set_wall_node_w(bx, Ww, c);
     }
 }
 
@@ -280,21 +361,20 @@ int grid_for(long long work, int threads)
 }  // namespace
 
 template <typename T>
-cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, cudaStream_t st)
+cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, float *Dn, cudaStream_t st)
 {
-    prep_kernel<T><<<grid_for(bx.np, 256), 256, 0, st>>>(bx, Q, W);
+    prep_kernel<T><<<grid_for(bx.np, 256), 256, 0, st>>>(bx, Q, W, Dn);
     return cudaGetLastError();
 }
 
-cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, cudaStream_t st, int *launches)
+cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, float *Dn, float *Wf, float *Ww, cudaStream_t st)
 {
     const long long faces = 2LL * ((long long)(bx.n[1] - 2) * (bx.n[2] - 2) + (long long)(bx.n[0] - 2) * (bx.n[2] - 2) +
                                    (long long)(bx.n[0] - 2) * (bx.n[1] - 2));
-    wall_face_kernel<<<grid_for(faces, 256), 256, 0, st>>>(bx, Q);
+    wall_face_kernel<<<grid_for(faces, 256), 256, 0, st>>>(bx, Q, Dn, Wf, Ww);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    wall_edge_corner_kernel<<<1, 512, 0, st>>>(bx, Q);
-    if (launches) *launches += 2;
+    wall_edge_corner_kernel<<<1, 512, 0, st>>>(bx, Q, Dn, Wf, Ww);
     return cudaGetLastError();
 }
 
@@ -321,6 +401,6 @@ cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partia
     return cudaGetLastError();
 }
 
-template cudaError_t launch_prep<float>(const BoxDev &, const double *, float *, cudaStream_t);
-template cudaError_t launch_prep<double>(const BoxDev &, const double *, double *, cudaStream_t);
+template cudaError_t launch_prep<float>(const BoxDev &, const double *, float *, float *, cudaStream_t);
+template cudaError_t launch_prep<double>(const BoxDev &, const double *, double *, float *, cudaStream_t);
 }  // namespace nopcs

@@ -43,9 +43,9 @@ struct VArgs {
     const T *R;
     int stage;
     double dt;
-    const double *Qn;
-    double *acc, *Qout;
-    T *Rout;
+    StageRegs<T> rg_out;
+    const double *rho_b64, *E_b64;        // mixed form: base state for the deviation of Q_n
+    float gm1;                            // gamma - 1
 };
 
 template <typename T>
@@ -168,6 +168,68 @@ __device__ __forceinline__ void add_div(const VArgs<T> &a, const Ring<T> &rg, in
     }
 }
 
+// primitives of a stage state from its FP32 deviation D = (rho', m_x, m_y, m_z, E')
+__device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, long long p, int kg, const float D[5])
+{
+    const long long np = a.np;
+    const float rho = a.rho_b[kg] + D[0];
+    const float ir = 1.0f / rho;
+    const float u = D[1] * ir, v = D[2] * ir, w = D[3] * ir;
+    const float ke = 0.5f * (D[1] * u + D[2] * v + D[3] * w);
+    const float pd = a.gm1 * (D[4] - ke);
+    float *Wn = a.rg_out.Wn;
+    Wn[p] = D[0];
+    Wn[np + p] = u;
+    Wn[2 * np + p] = v;
+    Wn[3 * np + p] = w;
+    Wn[4 * np + p] = pd;
+    Wn[5 * np + p] = D[4] + pd;
+}
+
+// Mixed form of the classical RK4 stage.  The slopes are FP32 (they are FP32
+// right-hand sides); K = k1 + 2 k2 + 2 k3 + k4 is accumulated in FP32 and added
+// to the FP64 state once, Q_n += dt/6 K, in FP64.  The stage states
+// Q_n + c dt k are formed as FP32 deviations from the hydrostatic base, the
+// same quantities the primitive recovery of the FP64 form rounds to FP32.
+__device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p, int kg, const float r[5])
+{
+    const long long np = a.np;
+    const int s = a.stage;
+    float K[5];
+    if (s == 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) K[k] = r[k];
+    } else {
+        const float w = s == 4 ? 1.0f : 2.0f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) K[k] = a.rg_out.Kacc[k * np + p] + w * r[k];
+    }
+    float D[5];
+    if (s < 4) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a.rg_out.Kacc[k * np + p] = K[k];
+        const float c = (float)(s == 3 ? a.dt : 0.5 * a.dt);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) D[k] = a.rg_out.Dn[k * np + p] + c * r[k];
+    } else {
+        const double w6 = a.dt / 6.0;
+        double q[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            q[k] = a.rg_out.Qn[k * np + p] + w6 * (double)K[k];
+            a.rg_out.Qn[k * np + p] = q[k];
+        }
+        D[0] = (float)(q[0] - a.rho_b64[kg]);
+        D[1] = (float)q[1];
+        D[2] = (float)q[2];
+        D[3] = (float)q[3];
+        D[4] = (float)(q[4] - a.E_b64[kg]);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a.rg_out.Dn[k * np + p] = D[k];
+    }
+    prim_from_dev(a, p, kg, D);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
 {
@@ -210,7 +272,9 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
             if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || o == 0 || o == nz - 1) r[1] = r[2] = r[3] = 0;
             if (a.stage == 0) {
 #pragma unroll
-                for (int k = 0; k < 5; ++k) a.Rout[k * np + p] = r[k];
+                for (int k = 0; k < 5; ++k) a.rg_out.Rout[k * np + p] = r[k];
+            } else if constexpr (sizeof(T) == 4) {
+                mixed_update(a, p, kg, r);
             } else {
                 // classical RK4: acc collects Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
                 const double bw = (a.stage == 1 || a.stage == 4) ? a.dt / 6.0 : a.dt / 3.0;
@@ -220,14 +284,14 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
                     const double rk = (double)r[k];
                     const long long i = k * np + p;
                     if (a.stage == 1) {
-                        const double q = a.Qn[i];
-                        a.acc[i] = q + bw * rk;
-                        a.Qout[i] = q + cw * rk;
+                        const double q = a.rg_out.Qn[i];
+                        a.rg_out.acc[i] = q + bw * rk;
+                        a.rg_out.Qout[i] = q + cw * rk;
                     } else if (a.stage < 4) {
-                        a.acc[i] = a.acc[i] + bw * rk;
-                        a.Qout[i] = a.Qn[i] + cw * rk;
+                        a.rg_out.acc[i] = a.rg_out.acc[i] + bw * rk;
+                        a.rg_out.Qout[i] = a.rg_out.Qn[i] + cw * rk;
                     } else {
-                        a.Qout[i] = a.acc[i] + bw * rk;
+                        a.rg_out.Qout[i] = a.rg_out.acc[i] + bw * rk;
                     }
                 }
             }
@@ -254,8 +318,8 @@ cudaError_t init_visc_kernels()
 }
 
 template <typename T>
-cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const double *Qn,
-                               double *acc, double *Qout, T *Rout, cudaStream_t st)
+cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
+                               cudaStream_t st)
 {
     VArgs<T> a{};
     for (int d = 0; d < 3; ++d) {
@@ -285,10 +349,10 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
     a.R = R;
     a.stage = stage;
     a.dt = bx.dt;
-    a.Qn = Qn;
-    a.acc = acc;
-    a.Qout = Qout;
-    a.Rout = Rout;
+    a.rg_out = g;
+    a.rho_b64 = bx.rho_b64;
+    a.E_b64 = bx.E_b64;
+    a.gm1 = (float)(bx.gamma - 1.0);
     const int gx = (bx.n[0] + TX - 1) / TX, gy = (bx.n[1] + TY - 1) / TY;
     // z chunk: enough blocks for the whole GPU, at least 8 planes per block
     const long long want = 152LL * 8;
@@ -302,9 +366,9 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
     return cudaGetLastError();
 }
 
-template cudaError_t launch_visc_update<float>(const BoxDev &, const float *, const float *, int, const double *,
-                                              double *, double *, float *, cudaStream_t);
+template cudaError_t launch_visc_update<float>(const BoxDev &, const float *, const float *, int,
+                                              const StageRegs<float> &, cudaStream_t);
 template cudaError_t launch_visc_update<double>(const BoxDev &, const double *, const double *, int,
-                                               const double *, double *, double *, double *, cudaStream_t);
+                                               const StageRegs<double> &, cudaStream_t);
 
 }  // namespace nopcs

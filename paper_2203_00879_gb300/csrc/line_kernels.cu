@@ -57,15 +57,44 @@ __device__ __forceinline__ const double *inv_ptr<double>(const LineOpDev &op) { 
 template <>
 __device__ __forceinline__ const float *inv_ptr<float>(const LineOpDev &op) { return op.inv32; }
 
+template <typename T>
+__device__ __forceinline__ T cp_limit(const LineOpDev &op) { return (T)op.cpL; }
+template <typename T>
+__device__ __forceinline__ T inv_limit(const LineOpDev &op) { return (T)op.invL; }
+
+// dot product of `len` taps with a column (stride LP), four partial sums
+template <typename T>
+__device__ __forceinline__ T dot_col(const T *c, const T *f, int len, int LP)
+{
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int k = 0;
+    for (; k + 4 <= len; k += 4) {
+        s0 += c[k] * f[(size_t)k * LP];
+        s1 += c[k + 1] * f[(size_t)(k + 1) * LP];
+        s2 += c[k + 2] * f[(size_t)(k + 2) * LP];
+        s3 += c[k + 3] * f[(size_t)(k + 3) * LP];
+    }
+    for (; k < len; ++k) s0 += c[k] * f[(size_t)k * LP];
+    return (s0 + s1) + (s2 + s3);
+}
+
 template <typename T, int MODE, int AXIS>
 __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
+    constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
     constexpr int W = MODE == MODE_FILTER ? 3 : 2;     // right-hand-side half-width
     constexpr int NEXP = MODE == MODE_FILTER ? 3 : 2;  // explicit rows at each wall
+    constexpr int U = 4;                               // loads in flight per thread and pass
     const int LINES = a.lines, LP = a.lines + 1, RT = a.rt;
+    const int KC = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
+    // shared memory: end-row taps (2 x max_taps), Thomas factors (2 x KC), tile
+    T *cs = reinterpret_cast<T *>(smraw);
+    T *ce = cs + op.max_taps;
+    T *tcp = ce + op.max_taps;
+    T *tiv = tcp + KC;
+    T *sm = tiv + KC;
     const int nx = a.n[0], ny = a.n[1];
     const long long np = a.np;
 
@@ -79,74 +108,88 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 
     const int *rec = op.sub + b * SUB_REC;
     const int s = rec[0], e = rec[1], tlo = rec[2], thi = rec[3];
+    const int j0s = rec[4], lens = rec[5], j0e = rec[7], lene = rec[8];
+    const int lo = rec[10], hi = rec[11];
     const int nrows = thi - tlo + 1;
     const long long srow = AXIS == 0 ? 1 : (AXIS == 1 ? (long long)nx : (long long)nx * ny);
     const long long sa = AXIS == 0 ? (long long)nx : 1;
     const long long sc = AXIS == 2 ? (long long)nx : (long long)nx * ny;
-    const long long gbase = (long long)cc * sc + (long long)a0 * sa;
+    const long long gbase = (long long)cc * sc + (long long)a0 * sa + (long long)tlo * srow;
     // which of (row, line, cc) is the coordinate along the gravity axis
     const int gsel = a.ga == AXIS ? 0 : (a.ga == (AXIS == 0 ? 1 : 0) ? 1 : 2);
-
-    // ---- stage rows [tlo, thi] of nl lines -----------------------------------
-    // U items per thread per pass: all their global loads are issued before
-    // any is used, so each thread keeps several loads in flight.
-    constexpr int U = 4;
-    constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
-    const int total = nrows * nl;
     const size_t fs = (size_t)RT * LP;
-    for (int q0 = threadIdx.x; q0 < total; q0 += U * blockDim.x) {
-        T v[U][NIN];
-        int rr[U], ll[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = q0 + u * blockDim.x;
-            rr[u] = -1;
-            if (q < total) {
-                int r, l;
-                if (AXIS == 0) {
-                    r = q % nrows;
-                    l = q / nrows;
-                } else {
-                    l = q % nl;
-                    r = q / nl;
-                }
-                rr[u] = r;
-                ll[u] = l;
-                const long long gi = gbase + (long long)(tlo + r) * srow + (long long)l * sa;
-#pragma unroll
-                for (int k = 0; k < NIN; ++k) v[u][k] = a.in[k * np + gi];
-            }
+
+    // ---- block constants: end-row taps and the unconverged Thomas factors ----
+    {
+        const T *coef = coef_ptr<T>(op);
+        for (int k = threadIdx.x; k < lens; k += blockDim.x) cs[k] = coef[rec[6] + k];
+        for (int k = threadIdx.x; k < lene; k += blockDim.x) ce[k] = coef[rec[9] + k];
+        const T *cpp = cp_ptr<T>(op), *ivp = inv_ptr<T>(op);
+        for (int k = threadIdx.x; k < KC; k += blockDim.x) {
+            tcp[k] = cpp[k];
+            tiv[k] = ivp[k];
         }
+    }
+
+    // ---- stage rows [tlo, thi] of nl lines into [field][row][line] -----------
+    // x: a warp walks the rows of one line (coalesced along x, transposed into
+    // the odd line pitch); y, z: consecutive threads take consecutive lines.
+    {
+        int r0, rstep, l0, lstep;
+        if (AXIS == 0) {
+            r0 = threadIdx.x & 31;
+            rstep = 32;
+            l0 = threadIdx.x >> 5;
+            lstep = blockDim.x >> 5;
+        } else {
+            l0 = threadIdx.x % LINES;
+            lstep = LINES;  // one line per thread
+            r0 = threadIdx.x / LINES;
+            rstep = blockDim.x / LINES;
+        }
+        for (int l = l0; l < nl; l += lstep) {
+            const T *src = a.in + gbase + (long long)l * sa;
+            T *dst = sm + l;
+            const int gl = gsel == 1 ? a0 + l : cc;
+            for (int r = r0; r < nrows; r += U * rstep) {
+                T v[U][NIN];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int r = rr[u], l = ll[u];
-            if (r < 0) continue;
-            T *dst = sm + (size_t)r * LP + l;
-            if constexpr (MODE == MODE_FIELD) {
-                dst[0] = v[u][0];
-            } else if constexpr (MODE == MODE_FLUX) {
-                const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
-                const T rho = a.b0[gk] + v[u][0];
-                const T uu = v[u][1], vv = v[u][2], ww = v[u][3], pp = v[u][4];
-                const T H = a.b1[gk] + v[u][5];
-                const T ud = AXIS == 0 ? uu : (AXIS == 1 ? vv : ww);
-                const T m = rho * ud;
-                T f1 = m * uu, f2 = m * vv, f3 = m * ww;
-                if (AXIS == 0) f1 += pp;
-                if (AXIS == 1) f2 += pp;
-                if (AXIS == 2) f3 += pp;
-                dst[0] = m;
-                dst[fs] = f1;
-                dst[2 * fs] = f2;
-                dst[3 * fs] = f3;
-                dst[4 * fs] = H * ud;
-            } else {  // FILTER on Q - base
-                const int gk = gsel == 0 ? tlo + r : (gsel == 1 ? a0 + l : cc);
-                dst[0] = v[u][0] - a.b0[gk];
-                dst[fs] = v[u][1];
-                dst[2 * fs] = v[u][2];
-                dst[3 * fs] = v[u][3];
-                dst[4 * fs] = v[u][4] - a.b1[gk];
+                for (int u = 0; u < U; ++u) {
+                    const int rr = r + u * rstep;
+                    if (rr < nrows) {
+                        const T *p = src + (long long)rr * srow;
+#pragma unroll
+                        for (int k = 0; k < NIN; ++k) v[u][k] = p[k * np];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int rr = r + u * rstep;
+                    if (rr >= nrows) continue;
+                    T *d = dst + (size_t)rr * LP;
+                    if constexpr (MODE == MODE_FIELD) {
+                        d[0] = v[u][0];
+                    } else if constexpr (MODE == MODE_FLUX) {
+                        const int gk = gsel == 0 ? tlo + rr : gl;
+                        const T rho = a.b0[gk] + v[u][0];
+                        const T uu = v[u][1], vv = v[u][2], ww = v[u][3], pp = v[u][4];
+                        const T H = a.b1[gk] + v[u][5];
+                        const T ud = AXIS == 0 ? uu : (AXIS == 1 ? vv : ww);
+                        const T m = rho * ud;
+                        d[0] = m;
+                        d[fs] = m * uu + (AXIS == 0 ? pp : T(0));
+                        d[2 * fs] = m * vv + (AXIS == 1 ? pp : T(0));
+                        d[3 * fs] = m * ww + (AXIS == 2 ? pp : T(0));
+                        d[4 * fs] = H * ud;
+                    } else {  // FILTER on Q - base
+                        const int gk = gsel == 0 ? tlo + rr : gl;
+                        d[0] = v[u][0] - a.b0[gk];
+                        d[fs] = v[u][1];
+                        d[2 * fs] = v[u][2];
+                        d[3 * fs] = v[u][3];
+                        d[4 * fs] = v[u][4] - a.b1[gk];
+                    }
+                }
             }
         }
     }
@@ -156,24 +199,11 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     const int l = threadIdx.x % LINES;
     const int fld = threadIdx.x / LINES;
     if (l < nl && fld < NF) {
-        T *col = sm + (size_t)fld * RT * LP + l;
-        auto F = [&](int row) -> T { return col[(size_t)(row - tlo) * LP]; };
-        const T *coef = coef_ptr<T>(op);
+        T *col = sm + (size_t)fld * fs + l;  // row r at col[(r - tlo) * LP]
         const int N = op.N;
-        // 1. end rows from the equivalent explicit scheme
-        T gs = 0, ge = 0;
-        {
-            const int j0 = rec[4], len = rec[5], off = rec[6];
-            T acc = 0;
-            for (int k = 0; k < len; ++k) acc += coef[off + k] * F(j0 + k);
-            gs = acc;
-        }
-        if (rec[8] > 0) {
-            const int j0 = rec[7], len = rec[8], off = rec[9];
-            T acc = 0;
-            for (int k = 0; k < len; ++k) acc += coef[off + k] * F(j0 + k);
-            ge = acc;
-        }
+        // 1. end rows from the equivalent explicit scheme (Eq. CS:fpCf_i)
+        const T gs = dot_col(cs, col + (size_t)(j0s - tlo) * LP, lens, LP);
+        const T ge = lene > 0 ? dot_col(ce, col + (size_t)(j0e - tlo) * LP, lene, LP) : T(0);
         // explicit wall-closure rows strictly inside the sub-domain
         T exL[NEXP], exH[NEXP];
 #pragma unroll
@@ -182,34 +212,39 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             exH[r] = 0;
             if (r > s && r < e) {
                 T acc = 0;
+#pragma unroll
                 for (int j = 0; j < 5; ++j)
-                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * F(j);
+                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * col[(size_t)(j - tlo) * LP];
                 exL[r] = acc;
             }
             const int rh = N - 1 - r;
             if (rh > s && rh < e) {
                 T acc = 0;
+#pragma unroll
                 for (int j = 0; j < 5; ++j)
-                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * F(N - 1 - j);
+                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * col[(size_t)(N - 1 - j - tlo) * LP];
                 exH[r] = (T)op.ex_sign * acc;
             }
         }
-        // 2./3. Thomas over the implicit rows lo..hi
-        const int lo = rec[10], hi = rec[11];
+        // 2./3. Thomas over the implicit rows lo..hi; forward values overwrite
+        // the staged inputs, which a register window of 2W+1 keeps
         if (lo <= hi) {
             const int m = hi - lo + 1;
             const T al = (T)op.alpha;
             const T gL = lo == s + 1 ? gs : exL[NEXP - 1];
             const T gR = hi == e - 1 ? ge : exH[NEXP - 1];
-            const T *cpp = cp_ptr<T>(op), *ivp = inv_ptr<T>(op);
             const T r0 = (T)op.rb[0], r1 = (T)op.rb[1], r2 = (T)op.rb[2], r3 = (T)op.rb[3];
+            const T cL = cp_limit<T>(op), iL = inv_limit<T>(op);
             T win[2 * W + 1];
+            const T *pin = col + (size_t)(lo - W - tlo) * LP;
 #pragma unroll
-            for (int j = 0; j < 2 * W; ++j) win[j] = F(lo - W + j);
+            for (int j = 0; j < 2 * W; ++j) win[j] = pin[(size_t)j * LP];
+            pin += (size_t)(2 * W) * LP;                // row lo + W
+            T *pout = col + (size_t)(lo - tlo) * LP;   // row lo
             T dprev = 0;
             for (int r = 0; r < m; ++r) {
-                const int i = lo + r;
-                win[2 * W] = F(i + W);
+                win[2 * W] = *pin;
+                pin += LP;
                 T rhs;
                 if constexpr (MODE == MODE_FILTER)
                     rhs = r0 * win[3] + r1 * (win[4] + win[2]) + r2 * (win[5] + win[1]) + r3 * (win[6] + win[0]);
@@ -217,22 +252,26 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                     rhs = r0 * (win[3] - win[1]) + r1 * (win[4] - win[0]);
                 if (r == 0) rhs -= al * gL;
                 if (r == m - 1) rhs -= al * gR;
-                const T dp = (rhs - al * dprev) * ivp[r];
-                col[(size_t)(i - tlo) * LP] = dp;
+                const T iv = r < KC ? tiv[r] : iL;
+                const T dp = (rhs - al * dprev) * iv;
+                *pout = dp;
+                pout += LP;
                 dprev = dp;
 #pragma unroll
                 for (int j = 0; j < 2 * W; ++j) win[j] = win[j + 1];
             }
             T x = dprev;
+            pout -= 2 * (size_t)LP;  // row hi - 1
             for (int r = m - 2; r >= 0; --r) {
-                T *p = col + (size_t)(lo + r - tlo) * LP;
-                x = *p - cpp[r] * x;
-                *p = x;
+                const T cpr = r < KC ? tcp[r] : cL;
+                x = *pout - cpr * x;
+                *pout = x;
+                pout -= LP;
             }
         }
         // explicit values into their rows
         col[(size_t)(s - tlo) * LP] = gs;
-        if (rec[8] > 0) col[(size_t)(e - tlo) * LP] = ge;
+        if (lene > 0) col[(size_t)(e - tlo) * LP] = ge;
 #pragma unroll
         for (int r = 0; r < NEXP; ++r) {
             if (r > s && r < e) col[(size_t)(r - tlo) * LP] = exL[r];
@@ -243,54 +282,60 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     __syncthreads();
 
     // ---- write the sub-domain's own rows ---------------------------------------
-    const int nown = e - s + 1;
-    const int tot2 = nown * nl;
-    for (int q0 = threadIdx.x; q0 < tot2; q0 += U * blockDim.x) {
-        long long gi[U];
-        int rr[U], ll[U];
-        T old[U][5];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = q0 + u * blockDim.x;
-            rr[u] = -1;
-            if (q < tot2) {
-                int r, l2;
-                if (AXIS == 0) {
-                    r = q % nown;
-                    l2 = q / nown;
-                } else {
-                    l2 = q % nl;
-                    r = q / nl;
-                }
-                rr[u] = r;
-                ll[u] = l2;
-                gi[u] = gbase + (long long)(s + r) * srow + (long long)l2 * sa;
+    {
+        const int nown = e - s + 1;
+        int r0, rstep, l0, lstep;
+        if (AXIS == 0) {
+            r0 = threadIdx.x & 31;
+            rstep = 32;
+            l0 = threadIdx.x >> 5;
+            lstep = blockDim.x >> 5;
+        } else {
+            l0 = threadIdx.x % LINES;
+            lstep = LINES;
+            r0 = threadIdx.x / LINES;
+            rstep = blockDim.x / LINES;
+        }
+        const long long obase = gbase + (long long)(s - tlo) * srow;
+        for (int ll = l0; ll < nl; ll += lstep) {
+            T *dstg = a.out + obase + (long long)ll * sa;
+            const T *srcs = sm + (size_t)(s - tlo) * LP + ll;
+            const int gl = gsel == 1 ? a0 + ll : cc;
+            for (int r = r0; r < nown; r += U * rstep) {
+                T old[U][5];
                 if (MODE == MODE_FLUX && !a.first) {
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) old[u][f] = a.out[f * np + gi[u]];
-                }
-            }
-        }
+                    for (int u = 0; u < U; ++u) {
+                        const int rr = r + u * rstep;
+                        if (rr < nown) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int r = rr[u];
-            if (r < 0) continue;
-            const T *src = sm + (size_t)(s - tlo + r) * LP + ll[u];
-            if constexpr (MODE == MODE_FIELD) {
-                a.out[gi[u]] = src[0] * a.scale;
-            } else if constexpr (MODE == MODE_FLUX) {
-#pragma unroll
-                for (int f = 0; f < 5; ++f) {
-                    const T v = -src[f * fs] * a.scale;
-                    a.out[f * np + gi[u]] = a.first ? v : old[u][f] + v;
+                            for (int f = 0; f < 5; ++f) old[u][f] = dstg[f * np + (long long)rr * srow];
+                        }
+                    }
                 }
-            } else {
-                const int gk = gsel == 0 ? s + r : (gsel == 1 ? a0 + ll[u] : cc);
-                a.out[gi[u]] = src[0] + a.b0[gk];
-                a.out[np + gi[u]] = src[fs];
-                a.out[2 * np + gi[u]] = src[2 * fs];
-                a.out[3 * np + gi[u]] = src[3 * fs];
-                a.out[4 * np + gi[u]] = src[4 * fs] + a.b1[gk];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int rr = r + u * rstep;
+                    if (rr >= nown) continue;
+                    const T *src = srcs + (size_t)rr * LP;
+                    T *o = dstg + (long long)rr * srow;
+                    if constexpr (MODE == MODE_FIELD) {
+                        o[0] = src[0] * a.scale;
+                    } else if constexpr (MODE == MODE_FLUX) {
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) {
+                            const T v = -src[f * fs] * a.scale;
+                            o[f * np] = a.first ? v : old[u][f] + v;
+                        }
+                    } else {
+                        const int gk = gsel == 0 ? s + rr : gl;
+                        o[0] = src[0] + a.b0[gk];
+                        o[np] = src[fs];
+                        o[2 * np] = src[2 * fs];
+                        o[3 * np] = src[3 * fs];
+                        o[4 * np] = src[4 * fs] + a.b1[gk];
+                    }
+                }
             }
         }
     }
@@ -313,7 +358,8 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
     a.rt = op.max_tile;
     a.lines = pick_lines(pref_lines, a.rt, NF, sizeof(T));
-    size_t smem = (size_t)NF * a.rt * (a.lines + 1) * sizeof(T);
+    const int kc = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
+    size_t smem = ((size_t)NF * a.rt * (a.lines + 1) + 2 * (size_t)op.max_taps + 2 * (size_t)kc) * sizeof(T);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int Na = AXIS == 0 ? a.n[1] : a.n[0];
     const int Nc = AXIS == 2 ? a.n[1] : a.n[2];
@@ -321,8 +367,11 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     long long nblk = (long long)op.nsub * a.ntile_a * Nc;
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    // at least 256 threads: the extra ones only stage and store, which keeps
+    // more loads in flight per SM
     int threads = a.lines * NF;
     threads = (threads + 31) / 32 * 32;
+    if (threads < 256) threads = 256;
     if (threads > 1024) return cudaErrorInvalidConfiguration;
     line_kernel<T, MODE, AXIS><<<(unsigned)nblk, threads, smem, st>>>(op, a);
     return cudaGetLastError();

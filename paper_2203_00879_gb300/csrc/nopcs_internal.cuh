@@ -34,11 +34,15 @@ struct LineOpHost {
     std::vector<int> sub;         // nsub * SUB_REC
     std::vector<double> coef;     // end-row taps
     std::vector<double> cp, inv;  // Thomas factors, maxm entries
+    int max_taps = 0;             // longest end row
+    int kconv64 = 0, kconv32 = 0; // factors of rows >= kconv equal the limit in that precision
 };
 
 // Device view passed by value to the line kernels.
 struct LineOpDev {
-    int N, nsub, nexp, maxm, max_tile;
+    int N, nsub, nexp, maxm, max_tile, max_taps;
+    int kconv64, kconv32;
+    double cpL, invL;  // limits of the Thomas factors
     double alpha;
     double rb[4];
     double ex[3][5];

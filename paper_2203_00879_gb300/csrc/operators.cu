@@ -265,6 +265,21 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
         op.inv[r] = 1.0 / den;
         op.cp[r] = op.alpha * op.inv[r];
     }
+    // The factors converge geometrically to the root of alpha c^2 - c + alpha = 0.
+    // Past kconv they equal the last tabulated value in that precision, so the
+    // kernels keep only the first kconv entries and a register limit.
+    op.kconv64 = mm;
+    while (op.kconv64 > 1 && op.cp[op.kconv64 - 2] == op.cp[mm - 1] && op.inv[op.kconv64 - 2] == op.inv[mm - 1])
+        --op.kconv64;
+    op.kconv32 = mm;
+    while (op.kconv32 > 1 && (float)op.cp[op.kconv32 - 2] == (float)op.cp[mm - 1] &&
+           (float)op.inv[op.kconv32 - 2] == (float)op.inv[mm - 1])
+        --op.kconv32;
+    for (int b = 0; b < op.nsub; ++b) {
+        const int *rec = &op.sub[(size_t)b * SUB_REC];
+        op.max_taps = rec[5] > op.max_taps ? rec[5] : op.max_taps;
+        op.max_taps = rec[8] > op.max_taps ? rec[8] : op.max_taps;
+    }
     return true;
 }
 
@@ -304,6 +319,11 @@ cudaError_t LineOpBuf::upload()
     dev.nexp = h.nexp;
     dev.maxm = h.maxm;
     dev.max_tile = h.max_tile;
+    dev.max_taps = h.max_taps;
+    dev.kconv64 = h.kconv64;
+    dev.kconv32 = h.kconv32;
+    dev.cpL = h.cp.back();
+    dev.invL = h.inv.back();
     dev.alpha = h.alpha;
     for (int i = 0; i < 4; ++i) dev.rb[i] = h.rb[i];
     memcpy(dev.ex, h.ex, sizeof(dev.ex));

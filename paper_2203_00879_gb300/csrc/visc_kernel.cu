@@ -6,17 +6,22 @@
 // divergence of nodal viscous fluxes, and each nodal flux needs second-order
 // explicit gradients of u, v, w, T at its node: a +-2 stencil (+-3 next to a
 // wall, where both operators are one-sided).  A block owns a TX x TY column
-// tile and marches along z; it keeps the primitives (u, v, w, T) of the seven
+// tile and marches along z, keeping the primitives (u, v, w, T) of the seven
 // planes o-3 .. o+3 around the output plane o, with a two-node x/y halo, in a
-// shared-memory ring, so every primitive is loaded from global memory once per
-// block and plane.  Each thread evaluates the six nodal fluxes its divergence
-// needs from shared memory, adds the gravity source to the convective
-// right-hand side accumulated by the sweeps, holds the momentum at zero on
-// wall nodes (no-slip) and applies the RK4 stage to the FP64 registers.
+// shared-memory ring; every primitive is loaded from global memory once per
+// block and plane.  For each plane the block then
+//   1. evaluates every nodal viscous flux once: E_v on the plane's tile plus
+//      a one-node x halo, F_v on the tile plus a one-node y halo, and G_v on
+//      the tile of the planes the z divergence needs, kept in a ring of four
+//      planes so each G_v plane is computed once and used twice;
+//   2. takes the divergence at its tile nodes, adds the gravity source to the
+//      convective right-hand side accumulated by the sweeps, holds momentum at
+//      zero on wall nodes (no-slip) and applies the RK4 stage.
+// The primitive loads of the next plane are issued during step 2.
 //
 // Tiles never start past n - TX, so every tile is at least min(n, TX) wide and
-// the one-sided wall stencils stay inside its halo; a tile that had to be
-// shifted back writes only the columns it owns.
+// the one-sided wall stencils stay inside it; a tile that had to be shifted
+// back writes only the columns it owns.
 #include <math.h>
 
 #include "nopcs_internal.cuh"
@@ -29,6 +34,7 @@ constexpr int TX = 32, TY = 8, HALO = 2;
 constexpr int PX = TX + 2 * HALO, PY = TY + 2 * HALO, PLANE = PX * PY;
 constexpr int RING = 7;   // planes o-3 .. o+3
 constexpr int NPF = 4;    // u, v, w, T
+constexpr int GSLOTS = 4; // planes of G_v kept
 
 template <typename T>
 struct VArgs {
@@ -95,77 +101,98 @@ __device__ void load_plane(const VArgs<T> &a, const Ring<T> &rg, int z)
     }
 }
 
-// second-order explicit derivative of primitive f along axis AX at node (x, y, z)
-template <int AX, typename T>
-__device__ __forceinline__ T grad(const VArgs<T> &a, const Ring<T> &rg, int f, int x, int y, int z)
-{
-    const int c = AX == 0 ? x : (AX == 1 ? y : z);
-    const int N = a.n[AX];
-    auto at = [&](int off) -> T {
-        return rg.at(f, x + (AX == 0 ? off : 0), y + (AX == 1 ? off : 0), z + (AX == 2 ? off : 0));
-    };
-    if (c == 0) return (T(-3) * at(0) + T(4) * at(1) - at(2)) * a.ih2[AX];
-    if (c == N - 1) return (T(3) * at(0) - T(4) * at(-1) + at(-2)) * a.ih2[AX];
-    return (at(1) - at(-1)) * a.ih2[AX];
-}
-
-// nodal viscous flux along axis D at node (x, y, z): (tau_D0, tau_D1, tau_D2, u_k tau_Dk - q_D)
-template <int D, typename T>
-__device__ __forceinline__ void nodal_flux(const VArgs<T> &a, const Ring<T> &rg, int x, int y, int z, T out[4])
-{
-    constexpr int E1 = (D + 1) % 3, E2 = (D + 2) % 3;  // the two other axes
-    const T Tn = rg.at(3, x, y, z);
-    const T mu = Tn * sqrt(Tn) * a.S1 / (Tn + a.S);   // Sutherland
-    const T mub = a.c0 * Tn + a.c1;                    // Eq. reg over mu_s
-    const T gD = grad<D>(a, rg, D, x, y, z);            // d u_D / d x_D
-    const T g1D = grad<D>(a, rg, E1, x, y, z);          // d u_E1 / d x_D
-    const T g2D = grad<D>(a, rg, E2, x, y, z);          // d u_E2 / d x_D
-    const T g11 = grad<E1>(a, rg, E1, x, y, z);         // d u_E1 / d x_E1
-    const T g22 = grad<E2>(a, rg, E2, x, y, z);         // d u_E2 / d x_E2
-    const T gD1 = grad<E1>(a, rg, D, x, y, z);          // d u_D / d x_E1
-    const T gD2 = grad<E2>(a, rg, D, x, y, z);          // d u_D / d x_E2
-    T tau[3];
-    // Eq. ge19 off the diagonal; Eqs. bv1-bv3 on it:
-    // (4/3 mu + mu_b/mu_s) on the normal strain, (-2/3 mu + mu_b/mu_s) on the other two
-    tau[E1] = mu * a.iRe * (g1D + gD1);
-    tau[E2] = mu * a.iRe * (g2D + gD2);
-    tau[D] = ((T(4) / T(3) * mu + mub) * gD + (T(-2) / T(3) * mu + mub) * (g11 + g22)) * a.iRe;
-    const int cD = D == 0 ? x : (D == 1 ? y : z);
-    T q = 0;
-    if (cD != 0 && cD != a.n[D] - 1) q = -mu * a.kq * grad<D>(a, rg, 3, x, y, z);  // Eq. ge20; adiabatic walls
-    out[0] = tau[0];
-    out[1] = tau[1];
-    out[2] = tau[2];
-    out[3] = rg.at(0, x, y, z) * tau[0] + rg.at(1, x, y, z) * tau[1] + rg.at(2, x, y, z) * tau[2] - q;
-}
-
-// adds d(nodal viscous flux along D)/dx_D at (x, y, z) to r[1..4]
-template <int D, typename T>
-__device__ __forceinline__ void add_div(const VArgs<T> &a, const Ring<T> &rg, int x, int y, int z, T r[5])
-{
-    const int c = D == 0 ? x : (D == 1 ? y : z);
-    const int N = a.n[D];
-    const T ih = a.ih2[D];
-    const int dx = D == 0, dy = D == 1, dz = D == 2;
-    T fa[4], fb[4], fc[4];
-    if (c == 0) {
-        nodal_flux<D>(a, rg, x, y, z, fa);
-        nodal_flux<D>(a, rg, x + dx, y + dy, z + dz, fb);
-        nodal_flux<D>(a, rg, x + 2 * dx, y + 2 * dy, z + 2 * dz, fc);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) r[1 + k] += (T(-3) * fa[k] + T(4) * fb[k] - fc[k]) * ih;
-    } else if (c == N - 1) {
-        nodal_flux<D>(a, rg, x, y, z, fa);
-        nodal_flux<D>(a, rg, x - dx, y - dy, z - dz, fb);
-        nodal_flux<D>(a, rg, x - 2 * dx, y - 2 * dy, z - 2 * dz, fc);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) r[1 + k] += (T(3) * fa[k] - T(4) * fb[k] + fc[k]) * ih;
-    } else {
-        nodal_flux<D>(a, rg, x + dx, y + dy, z + dz, fa);
-        nodal_flux<D>(a, rg, x - dx, y - dy, z - dz, fb);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) r[1 + k] += (fa[k] - fb[k]) * ih;
+// Second-order explicit derivatives of the primitives at one node of the
+// ring: central inside, one-sided (-3, 4, -1)/(2h) on a wall.
+// mode 0: central, 1: low wall (forward), 2: high wall (backward).
+template <typename T>
+struct Stencil {
+    const T *b0, *bm1, *bp1, *bm2, *bp2;  // field-0 bases of planes j, j-1, j+1, j-2, j+2
+    int off;                              // ly * PX + lx
+    int xm, ym, zm;
+    T ihx, ihy, ihz;                      // 1 / (2 h)
+    __device__ __forceinline__ T val(int f) const { return b0[f * PLANE + off]; }
+    __device__ __forceinline__ T dx(int f) const
+    {
+        const T *p = b0 + f * PLANE + off;
+        if (xm == 0) return (p[1] - p[-1]) * ihx;
+        if (xm == 1) return (T(-3) * p[0] + T(4) * p[1] - p[2]) * ihx;
+        return (T(3) * p[0] - T(4) * p[-1] + p[-2]) * ihx;
     }
+    __device__ __forceinline__ T dy(int f) const
+    {
+        const T *p = b0 + f * PLANE + off;
+        if (ym == 0) return (p[PX] - p[-PX]) * ihy;
+        if (ym == 1) return (T(-3) * p[0] + T(4) * p[PX] - p[2 * PX]) * ihy;
+        return (T(3) * p[0] - T(4) * p[-PX] + p[-2 * PX]) * ihy;
+    }
+    __device__ __forceinline__ T dz(int f) const
+    {
+        const int o = f * PLANE + off;
+        if (zm == 0) return (bp1[o] - bm1[o]) * ihz;
+        if (zm == 1) return (T(-3) * b0[o] + T(4) * bp1[o] - bp2[o]) * ihz;
+        return (T(3) * b0[o] - T(4) * bm1[o] + bm2[o]) * ihz;
+    }
+};
+
+__device__ __forceinline__ int wall_mode(int c, int n) { return c == 0 ? 1 : (c == n - 1 ? 2 : 0); }
+
+template <typename T>
+__device__ __forceinline__ void visc_coeffs(const VArgs<T> &a, T Tn, T &mu, T &mub)
+{
+    mu = Tn * sqrt(Tn) * a.S1 / (Tn + a.S);  // Sutherland
+    mub = a.c0 * Tn + a.c1;                   // Eq. reg over mu_s
+}
+
+// E_v (x) and F_v (y) at a node (Eqs. ge6, ge7, ge19, ge20, bv1, bv2);
+// the normal heat flux is zero on an adiabatic wall
+template <typename T>
+__device__ __forceinline__ void flux_xy(const VArgs<T> &a, const Stencil<T> &S, bool wantE, bool wantF, T E[4],
+                                        T F[4])
+{
+    const T u = S.val(0), v = S.val(1), w = S.val(2);
+    T mu, mub;
+    visc_coeffs(a, S.val(3), mu, mub);
+    const T ux = S.dx(0), vx = S.dx(1), uy = S.dy(0), vy = S.dy(1), wz = S.dz(2);
+    const T k43 = (T(4) / T(3) * mu + mub) * a.iRe, k23 = (T(-2) / T(3) * mu + mub) * a.iRe, ks = mu * a.iRe;
+    const T txy = ks * (uy + vx);
+    if (wantE) {
+        const T wx = S.dx(2), uz = S.dz(0);
+        const T txx = k43 * ux + k23 * (vy + wz);
+        const T txz = ks * (uz + wx);
+        const T qx = S.xm == 0 ? -mu * a.kq * S.dx(3) : T(0);
+        E[0] = txx;
+        E[1] = txy;
+        E[2] = txz;
+        E[3] = u * txx + v * txy + w * txz - qx;
+    }
+    if (wantF) {
+        const T wy = S.dy(2), vz = S.dz(1);
+        const T tyy = k43 * vy + k23 * (ux + wz);
+        const T tyz = ks * (vz + wy);
+        const T qy = S.ym == 0 ? -mu * a.kq * S.dy(3) : T(0);
+        F[0] = txy;
+        F[1] = tyy;
+        F[2] = tyz;
+        F[3] = u * txy + v * tyy + w * tyz - qy;
+    }
+}
+
+// G_v (z) at a node (Eqs. ge8, ge19, ge20, bv3)
+template <typename T>
+__device__ __forceinline__ void flux_z(const VArgs<T> &a, const Stencil<T> &S, T G[4])
+{
+    const T u = S.val(0), v = S.val(1), w = S.val(2);
+    T mu, mub;
+    visc_coeffs(a, S.val(3), mu, mub);
+    const T k43 = (T(4) / T(3) * mu + mub) * a.iRe, k23 = (T(-2) / T(3) * mu + mub) * a.iRe, ks = mu * a.iRe;
+    const T tzz = k43 * S.dz(2) + k23 * (S.dx(0) + S.dy(1));
+    const T txz = ks * (S.dz(0) + S.dx(2));
+    const T tyz = ks * (S.dz(1) + S.dy(2));
+    const T qz = S.zm == 0 ? -mu * a.kq * S.dz(3) : T(0);
+    G[0] = txz;
+    G[1] = tyz;
+    G[2] = tzz;
+    G[3] = u * txz + v * tyz + w * tzz - qz;
 }
 
 // primitives of a stage state from its FP32 deviation D = (rho', m_x, m_y, m_z, E')
@@ -234,30 +261,133 @@ template <typename T>
 __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int EW = TX + 2, FH = TY + 2;  // E_v row width, F_v rows (one-node halos)
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
     Ring<T> rg;
     rg.s = reinterpret_cast<T *>(smraw);
     rg.x0 = min(xs, max(nx - TX, 0));
     rg.y0 = min(ys, max(ny - TY, 0));
+    T *EV = rg.s + (size_t)RING * NPF * PLANE;  // [4][TY][EW], local x + 1
+    T *FV = EV + 4 * TY * EW;                   // [4][FH][TX], local y + 1
+    T *GV = FV + 4 * FH * TX;                   // [GSLOTS][4][TY][TX]
     const int z0 = blockIdx.z * a.zc, z1 = min(nz, z0 + a.zc);
-    const int x = rg.x0 + (int)(threadIdx.x % TX), y = rg.y0 + (int)(threadIdx.x / TX);
-    const bool own = x < nx && y < ny && x >= xs && y >= ys;
+    const int tx = (int)(threadIdx.x % TX), ty = (int)(threadIdx.x / TX);
+    const int x = rg.x0 + tx, y = rg.y0 + ty;
+    const bool in_dom = x < nx && y < ny;
+    const bool own = in_dom && x >= xs && y >= ys;
     const long long np = a.np;
+    // G_v planes are computed in increasing order; ghi is the last one, and
+    // the ring holds the GSLOTS planes up to it
+    int ghi = -1000;
 
-    for (int z = max(0, z0 - 3); z <= min(nz - 1, z0 + 2); ++z) load_plane(a, rg, z);
+    // stencil at local (lx, ly) of plane j
+    auto stencil_at = [&](int lx, int ly, int j) {
+        Stencil<T> S;
+        const int gx = rg.x0 + lx, gy = rg.y0 + ly;
+        S.b0 = rg.s + (size_t)(j % RING) * NPF * PLANE;
+        S.bm1 = j >= 1 ? rg.s + (size_t)((j - 1) % RING) * NPF * PLANE : S.b0;
+        S.bp1 = j + 1 < nz ? rg.s + (size_t)((j + 1) % RING) * NPF * PLANE : S.b0;
+        S.bm2 = j >= 2 ? rg.s + (size_t)((j - 2) % RING) * NPF * PLANE : S.b0;
+        S.bp2 = j + 2 < nz ? rg.s + (size_t)((j + 2) % RING) * NPF * PLANE : S.b0;
+        S.off = (ly + HALO) * PX + (lx + HALO);
+        S.xm = wall_mode(gx, nx);
+        S.ym = wall_mode(gy, ny);
+        S.zm = wall_mode(j, nz);
+        S.ihx = a.ih2[0];
+        S.ihy = a.ih2[1];
+        S.ihz = a.ih2[2];
+        return S;
+    };
+
+    for (int z = max(0, z0 - 3); z <= min(nz - 1, z0 + 3); ++z) load_plane(a, rg, z);
+    __syncthreads();
     for (int o = z0; o < z1; ++o) {
-        if (o + 3 < nz) load_plane(a, rg, o + 3);
+        // ---- 1. nodal viscous fluxes ------------------------------------------
+        if (in_dom) {
+            T E[4], F[4];
+            flux_xy(a, stencil_at(tx, ty, o), true, true, E, F);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                EV[(k * TY + ty) * EW + tx + 1] = E[k];
+                FV[(k * FH + ty + 1) * TX + tx] = F[k];
+            }
+        }
+        if (threadIdx.x < 2 * TY) {  // E_v on the x halo
+            const int side = threadIdx.x / TY, hy = threadIdx.x % TY;
+            const int lx = side ? TX : -1;
+            const int gx = rg.x0 + lx, gy = rg.y0 + hy;
+            if (gx >= 0 && gx < nx && gy < ny) {
+                T E[4], F[4];
+                flux_xy(a, stencil_at(lx, hy, o), true, false, E, F);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) EV[(k * TY + hy) * EW + lx + 1] = E[k];
+            }
+        } else if (threadIdx.x < 2 * TY + 2 * TX) {  // F_v on the y halo
+            const int t = threadIdx.x - 2 * TY;
+            const int side = t / TX, hx = t % TX;
+            const int ly = side ? TY : -1;
+            const int gx = rg.x0 + hx, gy = rg.y0 + ly;
+            if (gy >= 0 && gy < ny && gx < nx) {
+                T E[4], F[4];
+                flux_xy(a, stencil_at(hx, ly, o), false, true, E, F);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) FV[(k * FH + ly + 1) * TX + hx] = F[k];
+            }
+        }
+        // G_v planes the z divergence of plane o needs: o-1 and o+1, or
+        // o..o+2 / o-2..o on a wall; all of jlo..jlo+2 once computed
+        const int zw = wall_mode(o, nz);
+        const int jlo = zw == 1 ? o : (zw == 2 ? o - 2 : o - 1);
+        for (int j = max(ghi + 1, jlo); j <= jlo + 2; ++j) {
+            const int slot = j & (GSLOTS - 1);
+            ghi = j;
+            if (in_dom) {
+                T G[4];
+                flux_z(a, stencil_at(tx, ty, j), G);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) GV[((slot * 4 + k) * TY + ty) * TX + tx] = G[k];
+            }
+        }
         __syncthreads();
+        // ---- 2. divergence, source, RK stage; next plane's primitives ----------
         if (own) {
             const long long p = x + (long long)nx * (y + (long long)ny * o);
             T r[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) r[k] = a.R[k * np + p];
-            // divergence of the nodal viscous fluxes (same explicit operator)
-            add_div<0>(a, rg, x, y, o, r);
-            add_div<1>(a, rg, x, y, o, r);
-            add_div<2>(a, rg, x, y, o, r);
+            const int xm = wall_mode(x, nx), ym = wall_mode(y, ny);
+            const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
+            const int sa = (o - 1) & (GSLOTS - 1), sb = (o + 1) & (GSLOTS - 1), s0 = o & (GSLOTS - 1);
+            const int sbb = (o + 2) & (GSLOTS - 1), saa = (o - 2) & (GSLOTS - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T *e = EV + (k * TY + ty) * EW + tx + 1;
+                const T *f = FV + (k * FH + ty + 1) * TX + tx;
+                T dvx, dvy, dvz;
+                if (xm == 0)
+                    dvx = (e[1] - e[-1]) * ihx;
+                else if (xm == 1)
+                    dvx = (T(-3) * e[0] + T(4) * e[1] - e[2]) * ihx;
+                else
+                    dvx = (T(3) * e[0] - T(4) * e[-1] + e[-2]) * ihx;
+                if (ym == 0)
+                    dvy = (f[TX] - f[-TX]) * ihy;
+                else if (ym == 1)
+                    dvy = (T(-3) * f[0] + T(4) * f[TX] - f[2 * TX]) * ihy;
+                else
+                    dvy = (T(3) * f[0] - T(4) * f[-TX] + f[-2 * TX]) * ihy;
+                const int gi = (k * TY + ty) * TX + tx;
+                if (zw == 0)
+                    dvz = (GV[sb * 4 * TY * TX + gi] - GV[sa * 4 * TY * TX + gi]) * ihz;
+                else if (zw == 1)
+                    dvz = (T(-3) * GV[s0 * 4 * TY * TX + gi] + T(4) * GV[sb * 4 * TY * TX + gi] -
+                           GV[sbb * 4 * TY * TX + gi]) * ihz;
+                else
+                    dvz = (T(3) * GV[s0 * 4 * TY * TX + gi] - T(4) * GV[sa * 4 * TY * TX + gi] +
+                           GV[saa * 4 * TY * TX + gi]) * ihz;
+                r[1 + k] += dvx + dvy + dvz;
+            }
             // gravity source, Eq. ge8a
             const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : o);
             const T w0 = a.W[p];
@@ -296,6 +426,8 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
                 }
             }
         }
+        // plane o + 4 replaces o - 3, which no later plane needs
+        if (o + 4 < nz && o + 1 < z1) load_plane(a, rg, o + 4);
         __syncthreads();
     }
 }
@@ -303,7 +435,8 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
 template <typename T>
 size_t ring_bytes()
 {
-    return (size_t)RING * NPF * PLANE * sizeof(T);
+    return ((size_t)RING * NPF * PLANE + 4 * TY * (TX + 2) + 4 * (TY + 2) * TX + (size_t)GSLOTS * 4 * TY * TX) *
+           sizeof(T);
 }
 
 }  // namespace

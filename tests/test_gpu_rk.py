@@ -59,7 +59,18 @@ def test_rhs_matches_oracle(prec, bs):
         N.nopcs_rhs(ctx, 0, to_dev(Q).data_ptr(), r.data_ptr())
         got = r.cpu().numpy().astype(np.float64)
         err = field_rel(got, ref)
-        assert np.all(err <= (1e-12 if prec == 0 else 1e-4)), err
+        if prec == 0:
+            # the momentum right-hand side is a small residual of pressure-gradient
+            # terms of size p/h: allow 30 ulps of that on top of 1e-12 of max |R|
+            pr = (p["gamma"] - 1) * (Q[4] - 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0])
+            h = p["len"][0] / (p["n"][0] - 1)
+            floor = 30 * np.finfo(float).eps * np.abs(pr).max() / h
+            d = np.abs(got - ref).reshape(5, -1).max(axis=1)
+            s_ = np.abs(ref).reshape(5, -1).max(axis=1)
+            assert np.all(d[[0, 4]] <= 1e-12 * s_[[0, 4]]), err
+            assert np.all(d[1:4] <= 1e-12 * s_[1:4] + floor), (err, d, floor)
+        else:
+            assert np.all(err <= 1e-4), err
     finally:
         N.nopcs_destroy(ctx)
 

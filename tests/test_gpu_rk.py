@@ -219,3 +219,39 @@ def test_set_get_state_host_roundtrip():
         assert np.array_equal(q, back)
     finally:
         N.nopcs_destroy(ctx)
+
+
+_CFG2 = {}
+
+
+def _config2_reference(p):
+    key = tuple(sorted((k, str(v)) for k, v in p.items()))
+    if key not in _CFG2:
+        orc = oracle.Solver(p)
+        _CFG2[key] = orc.step(orc.initial_state(), 200)
+    return _CFG2[key]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_config2_128_200_steps(prec):
+    """The full-RK-step workload's parity case: 128^3 two-temperature box,
+    200 RK4 steps (filter after steps 50, 100, 150, 200), base-subtracted
+    formulation, FP64 oracle.  Mixed form <= 1e-5 field-relative; FP64 form
+    <= 1e-12 (momentum relative to rho c)."""
+    N = binding()
+    p = S.box_params((128, 128, 128), sub_n=(64, 64, 64), base_subtract=1, seed=2)
+    ctx = _ctx(N, p, prec)
+    try:
+        N.nopcs_rk_step(ctx, 200)
+        Q = _state(N, ctx, p)
+    finally:
+        N.nopcs_destroy(ctx)
+    ref = _config2_reference(p)
+    fr = field_rel(Q, ref)
+    print("config2 prec", prec, "field-relative L-inf", fr, "L2",
+          np.sqrt(((Q - ref) ** 2).reshape(5, -1).sum(1) / (ref ** 2).reshape(5, -1).sum(1)))
+    if prec == 1:
+        assert np.all(fr <= 1e-5), fr
+    else:
+        err = state_err(Q, ref, p)
+        assert np.all(err <= 1e-12), (err, fr)

@@ -233,9 +233,9 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             tr = json.load(f)
-        from paper_2203_00879_gb300.build import source_hash
+        from paper_2203_00879_gb300.build import KERNEL_FILES, source_hash
         ent = tr.get("mixed", {}).get(dom)
-        if ent and ent.get("source_hash") == source_hash():
+        if ent and ent.get("source_hash") == source_hash(KERNEL_FILES[dom]):
             traffic = ent["bytes_per_point"] * npts
     except Exception:
         traffic = None

@@ -63,13 +63,22 @@ if __name__ == "__main__":
     print(LIB)
 
 
-def source_hash() -> str:
-    """Content hash of the CUDA sources and headers (tags profiler counters)."""
+KERNEL_FILES = {
+    "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu"], "diagnostics": ["rk_kernels.cu"],
+    "sweep_x": ["line_kernels.cu"], "sweep_y": ["line_kernels.cu"], "sweep_z": ["line_kernels.cu"],
+    "filter": ["line_kernels.cu"], "visc_rk_update": ["visc_kernel.cu"],
+}
+
+
+def source_hash(files=None) -> str:
+    """Content hash of CUDA sources (all of them, or the named files plus the
+    internal header); tags profiler counters with the code they measured."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(os.listdir(CSRC))
-    for f in files:
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(CSRC, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    names = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    if files is not None:
+        names = sorted(set(files) | {"nopcs_internal.cuh"})
+    for f in names:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]

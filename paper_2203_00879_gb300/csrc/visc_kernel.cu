@@ -101,10 +101,70 @@ __device__ void load_plane(const VArgs<T> &a, const Ring<T> &rg, int z)
     }
 }
 
+// A plane load split in two halves: issue() starts the global loads of this
+// thread's nodes into registers, finish() computes T and writes the ring, so
+// the loads can be in flight while the thread does other work.
+constexpr int PL_PER_THREAD = (PLANE + TX * TY - 1) / (TX * TY);
+template <typename T>
+struct PlaneLoad {
+    T w0[PL_PER_THREAD], u[PL_PER_THREAD], v[PL_PER_THREAD], w[PL_PER_THREAD], w4[PL_PER_THREAD];
+    int kg[PL_PER_THREAD];
+    bool ok[PL_PER_THREAD];
+    int z;
+    __device__ __forceinline__ void issue(const VArgs<T> &a, const Ring<T> &rg, int zz)
+    {
+        z = zz;
+        const int nx = a.n[0], ny = a.n[1];
+#pragma unroll
+        for (int t = 0; t < PL_PER_THREAD; ++t) {
+            const int idx = threadIdx.x + t * TX * TY;
+            const int lx = idx % PX, ly = idx / PX;
+            const int gx = rg.x0 - HALO + lx, gy = rg.y0 - HALO + ly;
+            ok[t] = idx < PLANE && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+            if (ok[t]) {
+                const long long i = gx + (long long)nx * (gy + (long long)ny * z);
+                w0[t] = a.W[i];
+                u[t] = a.W[a.np + i];
+                v[t] = a.W[2 * a.np + i];
+                w[t] = a.W[3 * a.np + i];
+                w4[t] = a.W[4 * a.np + i];
+                kg[t] = a.ga == 0 ? gx : (a.ga == 1 ? gy : z);
+            }
+        }
+    }
+    __device__ __forceinline__ void finish(const VArgs<T> &a, const Ring<T> &rg) const
+    {
+#pragma unroll
+        for (int t = 0; t < PL_PER_THREAD; ++t) {
+            const int idx = threadIdx.x + t * TX * TY;
+            if (idx >= PLANE) continue;
+            T uu = 0, vv = 0, ww = 0, tt = 0;
+            if (ok[t]) {
+                uu = u[t];
+                vv = v[t];
+                ww = w[t];
+                if constexpr (sizeof(T) == 4) {
+                    const float rr = w0[t] * a.ir_b[kg[t]];
+                    tt = a.T_b[kg[t]] + __fdividef(a.T_b[kg[t]] * (w4[t] * a.ip_b[kg[t]] - rr), 1.0f + rr);
+                } else {
+                    tt = a.gm2 * (a.p_b[kg[t]] + w4[t]) / (a.rho_b[kg[t]] + w0[t]);
+                }
+            }
+            T *p = rg.s + (size_t)(z % RING) * NPF * PLANE + idx;
+            p[0] = uu;
+            p[PLANE] = vv;
+            p[2 * PLANE] = ww;
+            p[3 * PLANE] = tt;
+        }
+    }
+};
+
 // Second-order explicit derivatives of the primitives at one node of the
 // ring: central inside, one-sided (-3, 4, -1)/(2h) on a wall.
-// mode 0: central, 1: low wall (forward), 2: high wall (backward).
-template <typename T>
+// mode 0: central, 1: low wall (forward), 2: high wall (backward).  EDGE is
+// false for blocks whose nodes are all at least one node away from the x and
+// y walls, so only the z mode (uniform over a plane) is tested there.
+template <typename T, bool EDGE>
 struct Stencil {
     const T *b0, *bm1, *bp1, *bm2, *bp2;  // field-0 bases of planes j, j-1, j+1, j-2, j+2
     int off;                              // ly * PX + lx
@@ -114,14 +174,14 @@ struct Stencil {
     __device__ __forceinline__ T dx(int f) const
     {
         const T *p = b0 + f * PLANE + off;
-        if (xm == 0) return (p[1] - p[-1]) * ihx;
+        if (!EDGE || xm == 0) return (p[1] - p[-1]) * ihx;
         if (xm == 1) return (T(-3) * p[0] + T(4) * p[1] - p[2]) * ihx;
         return (T(3) * p[0] - T(4) * p[-1] + p[-2]) * ihx;
     }
     __device__ __forceinline__ T dy(int f) const
     {
         const T *p = b0 + f * PLANE + off;
-        if (ym == 0) return (p[PX] - p[-PX]) * ihy;
+        if (!EDGE || ym == 0) return (p[PX] - p[-PX]) * ihy;
         if (ym == 1) return (T(-3) * p[0] + T(4) * p[PX] - p[2 * PX]) * ihy;
         return (T(3) * p[0] - T(4) * p[-PX] + p[-2 * PX]) * ihy;
     }
@@ -139,14 +199,17 @@ __device__ __forceinline__ int wall_mode(int c, int n) { return c == 0 ? 1 : (c 
 template <typename T>
 __device__ __forceinline__ void visc_coeffs(const VArgs<T> &a, T Tn, T &mu, T &mub)
 {
-    mu = Tn * sqrt(Tn) * a.S1 / (Tn + a.S);  // Sutherland
-    mub = a.c0 * Tn + a.c1;                   // Eq. reg over mu_s
+    if constexpr (sizeof(T) == 4)
+        mu = __fdividef(Tn * Tn * rsqrtf(Tn) * a.S1, Tn + a.S);  // Sutherland, FP32 intrinsics
+    else
+        mu = Tn * sqrt(Tn) * a.S1 / (Tn + a.S);  // Sutherland
+    mub = a.c0 * Tn + a.c1;                       // Eq. reg over mu_s
 }
 
 // E_v (x) and F_v (y) at a node (Eqs. ge6, ge7, ge19, ge20, bv1, bv2);
 // the normal heat flux is zero on an adiabatic wall
-template <typename T>
-__device__ __forceinline__ void flux_xy(const VArgs<T> &a, const Stencil<T> &S, bool wantE, bool wantF, T E[4],
+template <typename T, bool EDGE>
+__device__ __forceinline__ void flux_xy(const VArgs<T> &a, const Stencil<T, EDGE> &S, bool wantE, bool wantF, T E[4],
                                         T F[4])
 {
     const T u = S.val(0), v = S.val(1), w = S.val(2);
@@ -178,8 +241,8 @@ __device__ __forceinline__ void flux_xy(const VArgs<T> &a, const Stencil<T> &S, 
 }
 
 // G_v (z) at a node (Eqs. ge8, ge19, ge20, bv3)
-template <typename T>
-__device__ __forceinline__ void flux_z(const VArgs<T> &a, const Stencil<T> &S, T G[4])
+template <typename T, bool EDGE>
+__device__ __forceinline__ void flux_z(const VArgs<T> &a, const Stencil<T, EDGE> &S, T G[4])
 {
     const T u = S.val(0), v = S.val(1), w = S.val(2);
     T mu, mub;
@@ -200,7 +263,7 @@ __device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, long long p
 {
     const long long np = a.np;
     const float rho = a.rho_b[kg] + D[0];
-    const float ir = 1.0f / rho;
+    const float ir = __fdividef(1.0f, rho);
     const float u = D[1] * ir, v = D[2] * ir, w = D[3] * ir;
     const float ke = 0.5f * (D[1] * u + D[2] * v + D[3] * w);
     const float pd = a.gm1 * (D[4] - ke);
@@ -218,7 +281,8 @@ __device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, long long p
 // to the FP64 state once, Q_n += dt/6 K, in FP64.  The stage states
 // Q_n + c dt k are formed as FP32 deviations from the hydrostatic base, the
 // same quantities the primitive recovery of the FP64 form rounds to FP32.
-__device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p, int kg, const float r[5])
+__device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p, int kg, const float r[5],
+                                             const float kold[5], const float dn[5])
 {
     const long long np = a.np;
     const int s = a.stage;
@@ -229,7 +293,7 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p,
     } else {
         const float w = s == 4 ? 1.0f : 2.0f;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) K[k] = a.rg_out.Kacc[k * np + p] + w * r[k];
+        for (int k = 0; k < 5; ++k) K[k] = kold[k] + w * r[k];
     }
     float D[5];
     if (s < 4) {
@@ -237,7 +301,7 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p,
         for (int k = 0; k < 5; ++k) a.rg_out.Kacc[k * np + p] = K[k];
         const float c = (float)(s == 3 ? a.dt : 0.5 * a.dt);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) D[k] = a.rg_out.Dn[k * np + p] + c * r[k];
+        for (int k = 0; k < 5; ++k) D[k] = dn[k] + c * r[k];
     } else {
         const double w6 = a.dt / 6.0;
         double q[5];
@@ -257,10 +321,9 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p,
     prim_from_dev(a, p, kg, D);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
+template <typename T, bool EDGE>
+__device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *smraw)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int EW = TX + 2, FH = TY + 2;  // E_v row width, F_v rows (one-node halos)
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
@@ -281,18 +344,26 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
     // the ring holds the GSLOTS planes up to it
     int ghi = -1000;
 
-    // stencil at local (lx, ly) of plane j
-    auto stencil_at = [&](int lx, int ly, int j) {
-        Stencil<T> S;
-        const int gx = rg.x0 + lx, gy = rg.y0 + ly;
-        S.b0 = rg.s + (size_t)(j % RING) * NPF * PLANE;
-        S.bm1 = j >= 1 ? rg.s + (size_t)((j - 1) % RING) * NPF * PLANE : S.b0;
-        S.bp1 = j + 1 < nz ? rg.s + (size_t)((j + 1) % RING) * NPF * PLANE : S.b0;
-        S.bm2 = j >= 2 ? rg.s + (size_t)((j - 2) % RING) * NPF * PLANE : S.b0;
-        S.bp2 = j + 2 < nz ? rg.s + (size_t)((j + 2) % RING) * NPF * PLANE : S.b0;
+    // ring slot of plane o (refreshed once per plane); plane o + d sits in slot
+    // so + d wrapped into 0..RING-1 for |d| <= 3
+    int so = 0;
+    auto base = [&](int d) {
+        int t = so + d;
+        t = t >= RING ? t - RING : (t < 0 ? t + RING : t);
+        return rg.s + (size_t)t * NPF * PLANE;
+    };
+    // stencil at local (lx, ly) of plane j = o + dz, |dz| <= 2 (planes outside
+    // the box are never dereferenced: the z mode picks the one-sided form)
+    auto stencil_at = [&](int lx, int ly, int dz, int j) {
+        Stencil<T, EDGE> S;
+        S.b0 = base(dz);
+        S.bm1 = base(dz - 1);
+        S.bp1 = base(dz + 1);
+        S.bm2 = base(dz >= -1 ? dz - 2 : dz);
+        S.bp2 = base(dz <= 1 ? dz + 2 : dz);
         S.off = (ly + HALO) * PX + (lx + HALO);
-        S.xm = wall_mode(gx, nx);
-        S.ym = wall_mode(gy, ny);
+        S.xm = EDGE ? wall_mode(rg.x0 + lx, nx) : 0;
+        S.ym = EDGE ? wall_mode(rg.y0 + ly, ny) : 0;
         S.zm = wall_mode(j, nz);
         S.ihx = a.ih2[0];
         S.ihy = a.ih2[1];
@@ -303,10 +374,11 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
     for (int z = max(0, z0 - 3); z <= min(nz - 1, z0 + 3); ++z) load_plane(a, rg, z);
     __syncthreads();
     for (int o = z0; o < z1; ++o) {
+        so = o % RING;
         // ---- 1. nodal viscous fluxes ------------------------------------------
         if (in_dom) {
             T E[4], F[4];
-            flux_xy(a, stencil_at(tx, ty, o), true, true, E, F);
+            flux_xy(a, stencil_at(tx, ty, 0, o), true, true, E, F);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 EV[(k * TY + ty) * EW + tx + 1] = E[k];
@@ -319,7 +391,7 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
             const int gx = rg.x0 + lx, gy = rg.y0 + hy;
             if (gx >= 0 && gx < nx && gy < ny) {
                 T E[4], F[4];
-                flux_xy(a, stencil_at(lx, hy, o), true, false, E, F);
+                flux_xy(a, stencil_at(lx, hy, 0, o), true, false, E, F);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) EV[(k * TY + hy) * EW + lx + 1] = E[k];
             }
@@ -330,7 +402,7 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
             const int gx = rg.x0 + hx, gy = rg.y0 + ly;
             if (gy >= 0 && gy < ny && gx < nx) {
                 T E[4], F[4];
-                flux_xy(a, stencil_at(hx, ly, o), false, true, E, F);
+                flux_xy(a, stencil_at(hx, ly, 0, o), false, true, E, F);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) FV[(k * FH + ly + 1) * TX + hx] = F[k];
             }
@@ -344,18 +416,34 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
             ghi = j;
             if (in_dom) {
                 T G[4];
-                flux_z(a, stencil_at(tx, ty, j), G);
+                flux_z(a, stencil_at(tx, ty, j - o, j), G);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) GV[((slot * 4 + k) * TY + ty) * TX + tx] = G[k];
             }
         }
         __syncthreads();
         // ---- 2. divergence, source, RK stage; next plane's primitives ----------
+        // plane o + 4 replaces o - 3, which no later plane needs
+        const bool next = o + 4 < nz && o + 1 < z1;
+        PlaneLoad<T> pl;
+        if (next) pl.issue(a, rg, o + 4);
         if (own) {
             const long long p = x + (long long)nx * (y + (long long)ny * o);
             T r[5];
+            float kd[5], dn[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) r[k] = a.R[k * np + p];
+            const T w0 = a.W[p];
+            if constexpr (sizeof(T) == 4) {
+                if (a.stage >= 2) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) kd[k] = a.rg_out.Kacc[k * np + p];
+                }
+                if (a.stage >= 1 && a.stage <= 3) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) dn[k] = a.rg_out.Dn[k * np + p];
+                }
+            }
             const int xm = wall_mode(x, nx), ym = wall_mode(y, ny);
             const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
             const int sa = (o - 1) & (GSLOTS - 1), sb = (o + 1) & (GSLOTS - 1), s0 = o & (GSLOTS - 1);
@@ -390,7 +478,6 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
             }
             // gravity source, Eq. ge8a
             const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : o);
-            const T w0 = a.W[p];
             const T rho = a.rho_b[kg] + w0;
             const T ug = rg.at(a.ga, x, y, o);
             const T sg = w0 * a.g;
@@ -404,7 +491,7 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
 #pragma unroll
                 for (int k = 0; k < 5; ++k) a.rg_out.Rout[k * np + p] = r[k];
             } else if constexpr (sizeof(T) == 4) {
-                mixed_update(a, p, kg, r);
+                mixed_update(a, p, kg, r, kd, dn);
             } else {
                 // classical RK4: acc collects Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
                 const double bw = (a.stage == 1 || a.stage == 4) ? a.dt / 6.0 : a.dt / 3.0;
@@ -426,10 +513,24 @@ __global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
                 }
             }
         }
-        // plane o + 4 replaces o - 3, which no later plane needs
-        if (o + 4 < nz && o + 1 < z1) load_plane(a, rg, o + 4);
+        if (next) pl.finish(a, rg);
         __syncthreads();
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    // blocks whose x and y ranges (with the one-node flux halo) stay off the
+    // walls take the branch-free stencils
+    const int nx = a.n[0], ny = a.n[1];
+    const int x0 = min((int)blockIdx.x * TX, max(nx - TX, 0)), y0 = min((int)blockIdx.y * TY, max(ny - TY, 0));
+    const bool edge = x0 - 1 <= 0 || x0 + TX >= nx - 1 || y0 - 1 <= 0 || y0 + TY >= ny - 1;
+    if (edge)
+        visc_rk_body<T, true>(a, smraw);
+    else
+        visc_rk_body<T, false>(a, smraw);
 }
 
 template <typename T>

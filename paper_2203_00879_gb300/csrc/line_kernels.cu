@@ -242,7 +242,9 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             pin += (size_t)(2 * W) * LP;                // row lo + W
             T *pout = col + (size_t)(lo - tlo) * LP;   // row lo
             T dprev = 0;
-            for (int r = 0; r < m; ++r) {
+            // one forward row: right-hand side from the window, minus the
+            // coupling `adj` to a known end value, then the elimination
+            auto fwd = [&](T iv, T adj) {
                 win[2 * W] = *pin;
                 pin += LP;
                 T rhs;
@@ -250,21 +252,35 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                     rhs = r0 * win[3] + r1 * (win[4] + win[2]) + r2 * (win[5] + win[1]) + r3 * (win[6] + win[0]);
                 else
                     rhs = r0 * (win[3] - win[1]) + r1 * (win[4] - win[0]);
-                if (r == 0) rhs -= al * gL;
-                if (r == m - 1) rhs -= al * gR;
-                const T iv = r < KC ? tiv[r] : iL;
-                const T dp = (rhs - al * dprev) * iv;
+                const T dp = (rhs - adj - al * dprev) * iv;
                 *pout = dp;
                 pout += LP;
                 dprev = dp;
 #pragma unroll
                 for (int j = 0; j < 2 * W; ++j) win[j] = win[j + 1];
-            }
+            };
+            // first row carries the left end value (and the right one if m == 1)
+            fwd(tiv[0], al * gL + (m == 1 ? al * gR : T(0)));
+            const int kmid = min(KC, m - 1);
+            int r = 1;
+#pragma unroll 4
+            for (; r < kmid; ++r) fwd(tiv[r], T(0));
+#pragma unroll 4
+            for (; r < m - 1; ++r) fwd(iL, T(0));
+            if (m > 1) fwd(m - 1 < KC ? tiv[m - 1] : iL, al * gR);
+            // back substitution from row hi - 1 down to lo
             T x = dprev;
             pout -= 2 * (size_t)LP;  // row hi - 1
-            for (int r = m - 2; r >= 0; --r) {
-                const T cpr = r < KC ? tcp[r] : cL;
-                x = *pout - cpr * x;
+            r = m - 2;
+#pragma unroll 4
+            for (; r >= KC; --r) {
+                x = *pout - cL * x;
+                *pout = x;
+                pout -= LP;
+            }
+#pragma unroll 4
+            for (; r >= 0; --r) {
+                x = *pout - tcp[r] * x;
                 *pout = x;
                 pout -= LP;
             }

@@ -233,6 +233,15 @@ nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double alpha_f, dou
                                  int *nsub, int *starts, int *end_j0, int *end_len,
                                  double *coef, int max_coef);
 
+/*
+ * Host evaluation of the same line operator, FP64, the arithmetic of the line
+ * kernels (end rows from C, Thomas with tabulated factors), for inspection and
+ * tests; needs no GPU.  f and g are host arrays of N doubles; g = L f
+ * (dimensionless: divide by h for a derivative).  Errors: EINVAL.
+ */
+nopcs_status nopcs_operator_apply(int N, int sub_n, int kind, double alpha_f, double thresh, const double *f,
+                                  double *g);
+
 #ifdef __cplusplus
 }
 #endif

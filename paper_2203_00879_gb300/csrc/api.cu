@@ -29,6 +29,7 @@ struct BoxRes {
     nopcs_box_desc d{};
     BoxDev dev{};
     LineOpBuf dop64[3], dop32[3], fop[3];
+    GemmOpBuf gop[3];  // dense blocks of the FP32 derivative (tensor-core form)
     bool mixed = false;
     double *Q = nullptr;
     void *W = nullptr, *R = nullptr;
@@ -62,6 +63,7 @@ struct nopcs_ctx {
     std::vector<BoxRes> boxes;
     std::string err;
     cudaGraphExec_t step_exec = nullptr;
+    int *dev_err = nullptr;  // set by kernels whose bounded waits gave up
     bool profiling = false;
     std::vector<ProfPair> pool;
     size_t pool_used = 0;
@@ -148,6 +150,7 @@ void free_box(BoxRes &b)
         b.dop64[a].release();
         b.dop32[a].release();
         b.fop[a].release();
+        b.gop[a].release();
     }
     if (b.Q) cudaFree(b.Q);
     if (b.W) cudaFree(b.W);
@@ -200,6 +203,10 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
         CK(b.dop64[a].upload(), "operator upload");
         CK(b.dop32[a].upload(), "operator upload");
         CK(b.fop[a].upload(), "operator upload");
+        if (ctx->form == NOPCS_FORM_GEMM_3XTF32) {
+            build_dense_blocks(b.dop32[a].host, b.gop[a].host);
+            CK(b.gop[a].upload(), "dense operator upload");
+        }
     }
     // base tables
     std::vector<double> rh, ph;
@@ -461,15 +468,18 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
         std::string m;
         if (!valid_box(boxes[i], m)) return fail(nullptr, NOPCS_EINVAL, "box " + std::to_string(i) + ": " + m);
     }
-    if (form == NOPCS_FORM_GEMM_3XTF32 || form == NOPCS_FORM_GEMM_BF16X3)
-        return fail(nullptr, NOPCS_EUNSUPPORTED, "GEMM solve forms are not built in this version");
+    if (form == NOPCS_FORM_GEMM_BF16X3)
+        return fail(nullptr, NOPCS_EUNSUPPORTED, "the BF16x3 tensor-core form is not built in this version");
     nopcs_ctx *ctx = new nopcs_ctx();
     ctx->prec = prec;
-    ctx->form = NOPCS_FORM_THOMAS;
+    ctx->form = form == NOPCS_FORM_GEMM_3XTF32 ? NOPCS_FORM_GEMM_3XTF32 : NOPCS_FORM_THOMAS;
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
     if (e == cudaSuccess) e = init_visc_kernels();
+    if (e == cudaSuccess && ctx->form == NOPCS_FORM_GEMM_3XTF32) e = init_gemm_kernels();
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dev_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         g_init_error = std::string("CUDA: ") + cudaGetErrorString(e);
@@ -507,6 +517,7 @@ void nopcs_destroy(nopcs_ctx *ctx)
         cudaEventDestroy(p.b);
     }
     for (auto &b : ctx->boxes) free_box(b);
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
@@ -579,17 +590,24 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
                 return fail(ctx, NOPCS_ENOMEM, "order-2 scratch");
             }
         }
-        cudaError_t e = dtype == 0 ? launch_line_field<double>(op, axis, b.dev.n, (const double *)f,
-                                                               (double *)b.scratch, scale, st)
-                                   : launch_line_field<float>(op, axis, b.dev.n, (const float *)f,
-                                                              (float *)b.scratch, scale, st);
+        cudaError_t e;
+        if (dtype == 1 && ctx->form == NOPCS_FORM_GEMM_3XTF32)
+            e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)f, (float *)b.scratch, scale,
+                                  ctx->dev_err, st);
+        else if (dtype == 0)
+            e = launch_line_field<double>(op, axis, b.dev.n, (const double *)f, (double *)b.scratch, scale, st);
+        else
+            e = launch_line_field<float>(op, axis, b.dev.n, (const float *)f, (float *)b.scratch, scale, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
         src = b.scratch;
     }
-    cudaError_t e = dtype == 0 ? launch_line_field<double>(op, axis, b.dev.n, (const double *)src, (double *)df,
-                                                           scale, st)
-                               : launch_line_field<float>(op, axis, b.dev.n, (const float *)src, (float *)df,
-                                                          scale, st);
+    cudaError_t e;
+    if (dtype == 1 && ctx->form == NOPCS_FORM_GEMM_3XTF32)
+        e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)src, (float *)df, scale, ctx->dev_err, st);
+    else if (dtype == 0)
+        e = launch_line_field<double>(op, axis, b.dev.n, (const double *)src, (double *)df, scale, st);
+    else
+        e = launch_line_field<float>(op, axis, b.dev.n, (const float *)src, (float *)df, scale, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
     return NOPCS_OK;
 }
@@ -687,6 +705,13 @@ nopcs_status nopcs_synchronize(nopcs_ctx *ctx)
 {
     if (!ctx) return NOPCS_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    int flag = 0;
+    CK(cudaMemcpy(&flag, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "synchronize");
+    if (flag) {
+        CK(cudaMemset(ctx->dev_err, 0, sizeof(int)), "synchronize");
+        return fail(ctx, NOPCS_ETIMEOUT, "a bounded wait for the tensor cores gave up");
+    }
     return NOPCS_OK;
 }
 

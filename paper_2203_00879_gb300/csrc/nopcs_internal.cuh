@@ -59,6 +59,42 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
                    std::string &msg);
 int partition_rule(int N, int sub_n, int *start);
 
+// FP64 host evaluation of a line operator (the arithmetic of the line kernels).
+void apply_line_host(const LineOpHost &op, const double *f, double *g);
+
+// Dense per-sub-domain operators for the tensor-core form.  Sub-domain b maps
+// its staging window [tile_lo, tile_lo + Kpad) to its n_b outputs:
+// g = D_b f_window.  D_b is stored as B operands of tcgen05.mma (N = outputs,
+// K = window), K-major, no swizzle, split into TF32 hi and lo parts:
+// element (n, k) of a block sits at float offset
+//   (n / 8) * (Kpad / 4) * 32 + (k / 4) * 32 + (n % 8) * 4 + (k % 4).
+struct DenseHost {
+    int N = 0, nsub = 0, max_npad = 0, max_kpad = 0;
+    std::vector<int> rec;       // per sub-domain: s, n_b, Npad, Kpad, window start, float offset
+    std::vector<float> hi, lo;  // concatenated blocks
+};
+constexpr int DENSE_REC = 6;
+void build_dense_blocks(const LineOpHost &op, DenseHost &out);
+
+// Device view of the dense blocks (tensor-core form).
+struct GemmOpDev {
+    int N, nsub, max_npad, max_kpad;
+    const int *rec;
+    const float *hi, *lo;
+};
+struct GemmOpBuf {
+    DenseHost host;
+    GemmOpDev dev{};
+    void *mem = nullptr;
+    cudaError_t upload();
+    void release();
+};
+cudaError_t init_gemm_kernels();
+// FP32 field derivative by the 3xTF32 tensor-core form; err <- 1 if a bounded
+// wait for the tensor cores gave up.
+cudaError_t launch_gemm_field(const GemmOpDev &op, int axis, const int n[3], const float *f, float *out,
+                              double scale, int *err, cudaStream_t st);
+
 // Owns the device copy of a LineOpHost.
 struct LineOpBuf {
     LineOpHost host;

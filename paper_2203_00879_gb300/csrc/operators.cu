@@ -18,6 +18,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "nopcs_internal.cuh"
 
 namespace nopcs {
@@ -283,6 +285,107 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
     return true;
 }
 
+void apply_line_host(const LineOpHost &op, const double *f, double *g)
+{
+    const int N = op.N;
+    const double al = op.alpha;
+    auto explicit_row = [&](int i) {
+        double acc = 0.0;
+        if (i < op.nexp) {
+            for (int j = 0; j < 5 && j < N; ++j) acc += op.ex[i][j] * f[j];
+        } else {
+            const int r = N - 1 - i;
+            for (int j = 0; j < 5 && j < N; ++j) acc += op.ex_sign * op.ex[r][j] * f[N - 1 - j];
+        }
+        return acc;
+    };
+    std::vector<double> dp;
+    for (int b = 0; b < op.nsub; ++b) {
+        const int *rec = &op.sub[(size_t)b * SUB_REC];
+        const int s = rec[0], e = rec[1], lo = rec[10], hi = rec[11];
+        double gs = 0.0, ge = 0.0;
+        for (int k = 0; k < rec[5]; ++k) gs += op.coef[rec[6] + k] * f[rec[4] + k];
+        for (int k = 0; k < rec[8]; ++k) ge += op.coef[rec[9] + k] * f[rec[7] + k];
+        for (int i = s + 1; i < e; ++i)
+            if (i < op.nexp || i > N - 1 - op.nexp) g[i] = explicit_row(i);
+        if (lo <= hi) {
+            const int m = hi - lo + 1;
+            const double gL = lo == s + 1 ? gs : g[op.nexp - 1];
+            const double gR = hi == e - 1 ? ge : g[N - op.nexp];
+            dp.assign(m, 0.0);
+            for (int r = 0; r < m; ++r) {
+                const int i = lo + r;
+                double rhs;
+                if (op.kind == KIND_DERIV)
+                    rhs = op.rb[0] * (f[i + 1] - f[i - 1]) + op.rb[1] * (f[i + 2] - f[i - 2]);
+                else
+                    rhs = op.rb[0] * f[i] + op.rb[1] * (f[i + 1] + f[i - 1]) + op.rb[2] * (f[i + 2] + f[i - 2]) +
+                          op.rb[3] * (f[i + 3] + f[i - 3]);
+                if (r == 0) rhs -= al * gL;
+                if (r == m - 1) rhs -= al * gR;
+                dp[r] = (rhs - al * (r ? dp[r - 1] : 0.0)) * op.inv[r];
+            }
+            double x = dp[m - 1];
+            g[hi] = x;
+            for (int r = m - 2; r >= 0; --r) {
+                x = dp[r] - op.cp[r] * x;
+                g[lo + r] = x;
+            }
+        }
+        g[s] = gs;
+        if (rec[8] > 0) g[e] = ge;
+    }
+}
+
+void build_dense_blocks(const LineOpHost &op, DenseHost &out)
+{
+    out = DenseHost();
+    out.N = op.N;
+    out.nsub = op.nsub;
+    out.rec.assign((size_t)op.nsub * DENSE_REC, 0);
+    const int N = op.N;
+    std::vector<double> f(N, 0.0), g(N, 0.0);
+    auto tf32 = [](float x) {
+        unsigned u;
+        memcpy(&u, &x, 4);
+        u &= 0xFFFFE000u;
+        float y;
+        memcpy(&y, &u, 4);
+        return y;
+    };
+    for (int b = 0; b < op.nsub; ++b) {
+        const int *rec = &op.sub[(size_t)b * SUB_REC];
+        const int s = rec[0], e = rec[1], tlo = rec[2], thi = rec[3];
+        const int nb = e - s + 1, K = thi - tlo + 1;
+        const int npad = (nb + 15) / 16 * 16, kpad = (K + 7) / 8 * 8;
+        int *r = &out.rec[(size_t)b * DENSE_REC];
+        r[0] = s;
+        r[1] = nb;
+        r[2] = npad;
+        r[3] = kpad;
+        r[4] = tlo;
+        r[5] = (int)out.hi.size();
+        out.max_npad = npad > out.max_npad ? npad : out.max_npad;
+        out.max_kpad = kpad > out.max_kpad ? kpad : out.max_kpad;
+        const size_t base = out.hi.size();
+        out.hi.resize(base + (size_t)npad * kpad, 0.0f);
+        out.lo.resize(base + (size_t)npad * kpad, 0.0f);
+        for (int k = 0; k < K; ++k) {
+            std::fill(f.begin(), f.end(), 0.0);
+            f[tlo + k] = 1.0;
+            apply_line_host(op, f.data(), g.data());
+            for (int n = 0; n < nb; ++n) {
+                const double d = g[s + n];
+                const float h = tf32((float)d);
+                const float l = tf32((float)(d - (double)h));
+                const size_t o = base + (size_t)(n / 8) * (kpad / 4) * 32 + (size_t)(k / 4) * 32 + (n % 8) * 4 + (k % 4);
+                out.hi[o] = h;
+                out.lo[o] = l;
+            }
+        }
+    }
+}
+
 cudaError_t LineOpBuf::upload()
 {
     release();
@@ -373,5 +476,17 @@ extern "C" nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double a
     if (starts) starts[op.nsub] = N;
     if (coef)
         for (size_t i = 0; i < op.coef.size(); ++i) coef[i] = op.coef[i];
+    return NOPCS_OK;
+}
+
+extern "C" nopcs_status nopcs_operator_apply(int N, int sub_n, int kind, double alpha_f, double thresh,
+                                             const double *f, double *g)
+{
+    if (kind != KIND_DERIV && kind != KIND_FILTER) return NOPCS_EINVAL;
+    if (!f || !g) return NOPCS_EINVAL;
+    LineOpHost op;
+    std::string msg;
+    if (!build_line_op(N, sub_n, kind, alpha_f, thresh, op, msg)) return NOPCS_EINVAL;
+    apply_line_host(op, f, g);
     return NOPCS_OK;
 }

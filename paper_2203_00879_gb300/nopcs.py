@@ -68,7 +68,8 @@ _L.nopcs_kernel_name.argtypes = [_i]
 _L.nopcs_kernel_name.restype = C.c_char_p
 _L.nopcs_operator_rows.argtypes = [_i, _i, _i, _d, _d, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
                                    C.POINTER(_i), C.POINTER(_d), _i]
-for _name in ("nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
+_L.nopcs_operator_apply.argtypes = [_i, _i, _i, _d, _d, C.c_void_p, C.c_void_p]
+for _name in ("nopcs_operator_apply", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
               "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows"):
@@ -199,3 +200,14 @@ def nopcs_operator_rows(N: int, sub_n: int, kind: int = 0, alpha_f: float = 0.13
         rows.append((j0[k], [coef[off + t] for t in range(L)]))
         off += L
     return list(starts[: nb + 1]), rows
+
+
+def nopcs_operator_apply(N: int, sub_n: int, f, kind: int = 0, alpha_f: float = 0.135, thresh: float = 1e-16):
+    """Host FP64 evaluation of the library's line operator on a numpy line f."""
+    import numpy as np
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.zeros_like(f)
+    st = _L.nopcs_operator_apply(N, sub_n, kind, alpha_f, thresh, f.ctypes.data, g.ctypes.data)
+    if st != NOPCS_OK:
+        raise NopcsError(st, "bad operator request")
+    return g

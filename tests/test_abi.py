@@ -94,3 +94,15 @@ def test_fp32_tables_have_24_taps_each_side(N):
     k = np.loadtxt(os.path.join(ROOT, "tests", "golden", "oucs3_equivalent_explicit_row.txt"))
     ref = k[24:73, 1]
     assert np.max(np.abs(np.array(c) - ref)) < 2e-16
+
+
+@pytest.mark.parametrize("Nn,sub_n", [(5, 3), (9, 4), (48, 24), (50, 24), (101, 24), (257, 64), (129, 0)])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_host_line_algorithm_matches_oracle(N, Nn, sub_n, kind):
+    """The library's own FP64 line algorithm (end rows, tabulated Thomas
+    factors) equals the oracle's NOHAP evaluation."""
+    rng = np.random.default_rng(Nn + 7 * sub_n + kind)
+    f = rng.standard_normal(Nn)
+    g = N.nopcs_operator_apply(Nn, sub_n, f, kind=kind)
+    ref = oracle.Op(Nn, kind=kind, sub_n=sub_n).nopcs(f)
+    assert np.max(np.abs(g - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))

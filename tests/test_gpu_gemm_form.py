@@ -1,0 +1,62 @@
+"""Parity of the tensor-core (3xTF32 tcgen05) form of nopcs_derivative with the
+FP64 oracle: FP32 fields, <= 1e-5 of max |f'| (order 1), 5e-5 (order 2)."""
+import numpy as np
+import pytest
+
+import nopcs_synth as S
+import oracle
+from gpu_util import binding, field_rel, stream_ptr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(N, n, sub_n):
+    p = S.box_params(n, sub_n=sub_n, perturb_amp=0.0)
+    return N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_GEMM_3XTF32, stream=stream_ptr()), p
+
+
+@pytest.mark.parametrize("n,sub_n", [((40, 36, 33), (16, 16, 16)), ((130, 66, 35), (64, 32, 8)),
+                                     ((200, 140, 129), (64, 64, 64)), ((7, 9, 11), (3, 4, 5))])
+def test_gemm_form_parity(n, sub_n):
+    import torch
+    N = binding()
+    ctx, p = _ctx(N, n, sub_n)
+    try:
+        f = S.sine_field(n, kmax=16, seed=7, noise=1e-3)
+        fd = to_dev(f, np.float32)
+        fin = fd.cpu().numpy().astype(np.float64)
+        h = p["len"][0] / (n[0] - 1)
+        out = torch.empty_like(fd)
+        for axis in range(3):
+            for order in (1, 2):
+                out.fill_(float("nan"))
+                N.nopcs_derivative(ctx, 0, axis, order, 1, fd.data_ptr(), out.data_ptr(), stream_ptr())
+                N.nopcs_synchronize(ctx)
+                got = out.cpu().numpy().astype(np.float64)
+                ref = oracle.deriv3d(fin, axis, h, sub_n[axis])
+                if order == 2:
+                    ref = oracle.deriv3d(ref, axis, h, sub_n[axis])
+                err = field_rel(got[None], ref[None])[0]
+                print("gemm parity", n, sub_n, "axis", axis, "order", order, "err %.3e" % err)
+                assert np.all(np.isfinite(got)), (axis, order)
+                assert err <= (1e-5 if order == 1 else 5e-5), (axis, order, err)
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def test_gemm_form_fp64_fields_use_thomas():
+    """FP64 fields keep the Thomas form under a tensor-core context (<= 1e-12)."""
+    import torch
+    N = binding()
+    n = (40, 36, 33)
+    ctx, p = _ctx(N, n, (16, 16, 16))
+    try:
+        f = S.sine_field(n, kmax=8, seed=3, noise=0.0)
+        fd = to_dev(f)
+        out = torch.empty_like(fd)
+        N.nopcs_derivative(ctx, 0, 1, 1, 0, fd.data_ptr(), out.data_ptr(), stream_ptr())
+        N.nopcs_synchronize(ctx)
+        ref = oracle.deriv3d(f, 1, p["len"][0] / 39, 16)
+        assert field_rel(out.cpu().numpy()[None], ref[None])[0] <= 1e-12
+    finally:
+        N.nopcs_destroy(ctx)

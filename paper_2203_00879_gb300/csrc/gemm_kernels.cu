@@ -52,7 +52,13 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
 }
 
-__device__ __forceinline__ float tf32_part(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// nearest TF32 value (round to nearest, ties away), kept in an FP32 container
+__device__ __forceinline__ float tf32_part(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
@@ -124,13 +130,17 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
     const long long sa = AXIS == 0 ? (long long)nx : 1;
     const long long sc = AXIS == 2 ? (long long)nx : (long long)nx * ny;
     const long long gbase = (long long)cc * sc + (long long)a0 * sa;
+    // Every row of D_b sums to zero (the operator annihilates constants), so
+    // each line's window is shifted by its value at the sub-domain start before
+    // the split: the same result, with less cancellation in the contraction.
     if (AXIS == 0) {
         // rows are contiguous: consecutive threads read consecutive points of a line
         const int tot = GM * kpad;
         for (int q = tid; q < tot; q += GM) {
             const int m = q / kpad, k = q % kpad;
             const int pos = wlo + k;
-            const float v = (m < nl && pos < N) ? f[gbase + (long long)m * sa + pos] : 0.0f;
+            const float c0 = m < nl ? f[gbase + (long long)m * sa + s] : 0.0f;
+            const float v = (m < nl && pos < N) ? f[gbase + (long long)m * sa + pos] - c0 : 0.0f;
             const float h = tf32_part(v), l = tf32_part(v - h);
             const uint32_t o = (uint32_t)(m >> 3) * sboA + (uint32_t)(k >> 2) * 128u + (m & 7) * 16u + (k & 3) * 4u;
             *reinterpret_cast<float *>(Ahi + o) = h;
@@ -139,12 +149,13 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
     } else {
         // thread m owns line a0 + m; a warp's loads of one position are coalesced
         const int m = tid;
+        const float c0 = m < nl ? f[gbase + (long long)s * srow + m] : 0.0f;
         for (int k4 = 0; k4 < kpad; k4 += 4) {
             float v[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int pos = wlo + k4 + t;
-                v[t] = (m < nl && pos < N) ? f[gbase + (long long)pos * srow + m] : 0.0f;
+                v[t] = (m < nl && pos < N) ? f[gbase + (long long)pos * srow + m] - c0 : 0.0f;
             }
             float4 h, l;
             h.x = tf32_part(v[0]);

@@ -345,10 +345,11 @@ void build_dense_blocks(const LineOpHost &op, DenseHost &out)
     out.rec.assign((size_t)op.nsub * DENSE_REC, 0);
     const int N = op.N;
     std::vector<double> f(N, 0.0), g(N, 0.0);
+    // nearest TF32 value (ties away from zero), as cvt.rna.tf32.f32
     auto tf32 = [](float x) {
         unsigned u;
         memcpy(&u, &x, 4);
-        u &= 0xFFFFE000u;
+        u = (u + 0x1000u) & 0xFFFFE000u;
         float y;
         memcpy(&y, &u, 4);
         return y;

@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=128, help="oracle sample grid for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle sample steps for the CPU baseline")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="rk", choices=["rk", "deriv"],
+                    help="rk: the RK-step benchmark (default); deriv: the derivative microbenchmark")
     return ap.parse_args()
 
 
@@ -169,10 +171,81 @@ def run_reference(args):
     return 0
 
 
+def run_deriv_microbench(args):
+    """NOHAP first derivative of a seeded 512^3 field (random-phase sines plus
+    N(0, 1e-3^2) noise) along x, y, z: Thomas form in FP64 and FP32 and the
+    3xTF32 tensor-core form, sub-domains of 32, 64 and 128.  Each case is timed
+    with CUDA events over `steps` calls after `warmup`; the field (0.5-1 GB) is
+    larger than L2."""
+    import torch
+    import nopcs_synth as S
+    from paper_2203_00879_gb300 import build as B
+    B.build()
+    from paper_2203_00879_gb300 import nopcs as N
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = 512
+    hbm, peak_kind = peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        tf32_peak, tf32_kind = bf16 * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16 ratio"
+    except Exception:
+        tf32_peak, tf32_kind = 1900.0 * 1.1 / 2.25, "fallback"
+    st = torch.cuda.current_stream()
+    px, py, pz = [torch.from_numpy(v).cuda() for v in S.sine_profiles((n, n, n), kmax=64, seed=7)]
+    g = torch.Generator(device="cuda").manual_seed(11)
+    f64 = (pz[:, None, None] + py[None, :, None] + px[None, None, :]).contiguous()
+    f64 += 1e-3 * torch.randn(f64.shape, generator=g, device="cuda", dtype=torch.float64)
+    f32 = f64.float()
+    rows = []
+    for sub_n in (32, 64, 128):
+        p = box(n, sub_n, perturb_amp=0.0)
+        for form_name, form in (("thomas", N.NOPCS_FORM_THOMAS), ("gemm_3xtf32", N.NOPCS_FORM_GEMM_3XTF32)):
+            ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, form=form, stream=st.cuda_stream)
+            cases = [("f32", 1, f32)] if form_name != "thomas" else [("f64", 0, f64), ("f32", 1, f32)]
+            for dname, dt, f in cases:
+                out = torch.empty_like(f)
+                for axis in range(3):
+                    for _ in range(args.warmup):
+                        N.nopcs_derivative(ctx, 0, axis, 1, dt, f.data_ptr(), out.data_ptr(), st.cuda_stream)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(st)
+                    for _ in range(args.steps):
+                        N.nopcs_derivative(ctx, 0, axis, 1, dt, f.data_ptr(), out.data_ptr(), st.cuda_stream)
+                    e1.record(st)
+                    N.nopcs_synchronize(ctx)
+                    ms = e0.elapsed_time(e1) / args.steps
+                    es = 8 if dt == 0 else 4
+                    gbs = 2 * es * n ** 3 / (ms * 1e-3) / 1e9
+                    row = {"form": form_name, "dtype": dname, "sub_n": sub_n, "axis": "xyz"[axis], "ms": ms,
+                           "points_per_s": n ** 3 / (ms * 1e-3), "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
+                    if form_name != "thomas":
+                        kpad = (sub_n + 48 + 7) // 8 * 8
+                        tflops = 6.0 * kpad * n ** 3 / (ms * 1e-3) / 1e12
+                        row.update({"tensor_tflops": tflops, "tensor_frac": tflops / tf32_peak})
+                    rows.append(row)
+            N.nopcs_destroy(ctx)
+    best = max(rows, key=lambda r: r["points_per_s"] if r["dtype"] == "f32" else 0)
+    line = {"metric": "NOHAP first-derivative points/s at 512^3 (microbenchmark)", "value": best["points_per_s"],
+            "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "seeded 512^3 sine+noise field, first derivative along x, y, z", "best": best,
+                       "l2": "inputs larger than L2 (512^3 FP32 = 0.54 GB)"},
+            "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s", "peak_kind": peak_kind,
+                         "tensor_peak_tflops": tf32_peak, "tensor_peak_kind": tf32_kind},
+            "cases": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "deriv":
+        return run_deriv_microbench(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -102,33 +102,42 @@ __device__ void load_plane(const VArgs<T> &a, const Ring<T> &rg, int z)
 }
 
 // A plane load split in two halves: issue() starts the global loads of this
-// thread's nodes into registers, finish() computes T and writes the ring, so
-// the loads can be in flight while the thread does other work.
+// thread's ring nodes into registers, finish() computes T and writes the ring,
+// so the loads are in flight while the thread does other work.  The in-plane
+// part of each node's address is fixed per block and computed once.
 constexpr int PL_PER_THREAD = (PLANE + TX * TY - 1) / (TX * TY);
 template <typename T>
 struct PlaneLoad {
+    int goff[PL_PER_THREAD];  // gx + nx * gy, or -1 outside the box / ring
+    int kgxy[PL_PER_THREAD];  // gravity coordinate when gravity is along x or y
     T w0[PL_PER_THREAD], u[PL_PER_THREAD], v[PL_PER_THREAD], w[PL_PER_THREAD], w4[PL_PER_THREAD];
-    int kg[PL_PER_THREAD];
-    bool ok[PL_PER_THREAD];
     int z;
-    __device__ __forceinline__ void issue(const VArgs<T> &a, const Ring<T> &rg, int zz)
+    __device__ __forceinline__ void init(const VArgs<T> &a, const Ring<T> &rg)
     {
-        z = zz;
         const int nx = a.n[0], ny = a.n[1];
 #pragma unroll
         for (int t = 0; t < PL_PER_THREAD; ++t) {
             const int idx = threadIdx.x + t * TX * TY;
             const int lx = idx % PX, ly = idx / PX;
             const int gx = rg.x0 - HALO + lx, gy = rg.y0 - HALO + ly;
-            ok[t] = idx < PLANE && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-            if (ok[t]) {
-                const long long i = gx + (long long)nx * (gy + (long long)ny * z);
+            const bool ok = idx < PLANE && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+            goff[t] = ok ? gx + nx * gy : -1;
+            kgxy[t] = a.ga == 0 ? gx : gy;
+        }
+    }
+    __device__ __forceinline__ void issue(const VArgs<T> &a, int zz)
+    {
+        z = zz;
+        const long long zo = (long long)a.n[0] * a.n[1] * zz;
+#pragma unroll
+        for (int t = 0; t < PL_PER_THREAD; ++t) {
+            if (goff[t] >= 0) {
+                const long long i = zo + goff[t];
                 w0[t] = a.W[i];
                 u[t] = a.W[a.np + i];
                 v[t] = a.W[2 * a.np + i];
                 w[t] = a.W[3 * a.np + i];
                 w4[t] = a.W[4 * a.np + i];
-                kg[t] = a.ga == 0 ? gx : (a.ga == 1 ? gy : z);
             }
         }
     }
@@ -139,15 +148,16 @@ struct PlaneLoad {
             const int idx = threadIdx.x + t * TX * TY;
             if (idx >= PLANE) continue;
             T uu = 0, vv = 0, ww = 0, tt = 0;
-            if (ok[t]) {
+            if (goff[t] >= 0) {
+                const int kg = a.ga == 2 ? z : kgxy[t];
                 uu = u[t];
                 vv = v[t];
                 ww = w[t];
                 if constexpr (sizeof(T) == 4) {
-                    const float rr = w0[t] * a.ir_b[kg[t]];
-                    tt = a.T_b[kg[t]] + __fdividef(a.T_b[kg[t]] * (w4[t] * a.ip_b[kg[t]] - rr), 1.0f + rr);
+                    const float rr = w0[t] * a.ir_b[kg];
+                    tt = a.T_b[kg] + __fdividef(a.T_b[kg] * (w4[t] * a.ip_b[kg] - rr), 1.0f + rr);
                 } else {
-                    tt = a.gm2 * (a.p_b[kg[t]] + w4[t]) / (a.rho_b[kg[t]] + w0[t]);
+                    tt = a.gm2 * (a.p_b[kg] + w4[t]) / (a.rho_b[kg] + w0[t]);
                 }
             }
             T *p = rg.s + (size_t)(z % RING) * NPF * PLANE + idx;
@@ -344,23 +354,29 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     // the ring holds the GSLOTS planes up to it
     int ghi = -1000;
 
-    // ring slot of plane o (refreshed once per plane); plane o + d sits in slot
-    // so + d wrapped into 0..RING-1 for |d| <= 3
-    int so = 0;
-    auto base = [&](int d) {
-        int t = so + d;
-        t = t >= RING ? t - RING : (t < 0 ? t + RING : t);
-        return rg.s + (size_t)t * NPF * PLANE;
+    // ring bases of planes o-3 .. o+3, refreshed once per plane (plane o + d
+    // sits in slot (o + d) mod RING)
+    const T *pb0, *pb1, *pb2, *pb3, *pb4, *pb5, *pb6;
+    auto pbase = [&](int k) -> const T * {  // k = d + 3, 0..6
+        switch (k) {
+        case 0: return pb0;
+        case 1: return pb1;
+        case 2: return pb2;
+        case 3: return pb3;
+        case 4: return pb4;
+        case 5: return pb5;
+        default: return pb6;
+        }
     };
     // stencil at local (lx, ly) of plane j = o + dz, |dz| <= 2 (planes outside
     // the box are never dereferenced: the z mode picks the one-sided form)
     auto stencil_at = [&](int lx, int ly, int dz, int j) {
         Stencil<T, EDGE> S;
-        S.b0 = base(dz);
-        S.bm1 = base(dz - 1);
-        S.bp1 = base(dz + 1);
-        S.bm2 = base(dz >= -1 ? dz - 2 : dz);
-        S.bp2 = base(dz <= 1 ? dz + 2 : dz);
+        S.b0 = pbase(dz + 3);
+        S.bm1 = pbase(dz + 2);
+        S.bp1 = pbase(dz + 4);
+        S.bm2 = pbase(dz >= -1 ? dz + 1 : dz + 3);
+        S.bp2 = pbase(dz <= 1 ? dz + 5 : dz + 3);
         S.off = (ly + HALO) * PX + (lx + HALO);
         S.xm = EDGE ? wall_mode(rg.x0 + lx, nx) : 0;
         S.ym = EDGE ? wall_mode(rg.y0 + ly, ny) : 0;
@@ -371,10 +387,29 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         return S;
     };
 
-    for (int z = max(0, z0 - 3); z <= min(nz - 1, z0 + 3); ++z) load_plane(a, rg, z);
+    PlaneLoad<T> pl;
+    pl.init(a, rg);
+    for (int z = max(0, z0 - 3); z <= min(nz - 1, z0 + 3); ++z) {
+        pl.issue(a, z);
+        pl.finish(a, rg);
+    }
     __syncthreads();
     for (int o = z0; o < z1; ++o) {
-        so = o % RING;
+        {
+            const int so = o % RING;
+            auto sb = [&](int d) {
+                int t = so + d;
+                t = t >= RING ? t - RING : (t < 0 ? t + RING : t);
+                return (const T *)(rg.s + (size_t)t * NPF * PLANE);
+            };
+            pb0 = sb(-3);
+            pb1 = sb(-2);
+            pb2 = sb(-1);
+            pb3 = sb(0);
+            pb4 = sb(1);
+            pb5 = sb(2);
+            pb6 = sb(3);
+        }
         // ---- 1. nodal viscous fluxes ------------------------------------------
         if (in_dom) {
             T E[4], F[4];
@@ -425,8 +460,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         // ---- 2. divergence, source, RK stage; next plane's primitives ----------
         // plane o + 4 replaces o - 3, which no later plane needs
         const bool next = o + 4 < nz && o + 1 < z1;
-        PlaneLoad<T> pl;
-        if (next) pl.issue(a, rg, o + 4);
+        if (next) pl.issue(a, o + 4);
         if (own) {
             const long long p = x + (long long)nx * (y + (long long)ny * o);
             T r[5];

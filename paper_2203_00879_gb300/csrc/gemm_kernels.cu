@@ -27,6 +27,7 @@ namespace nopcs {
 namespace {
 
 constexpr int GM = 128;       // lines per block (MMA M)
+constexpr int KC = 32;        // window points per pipeline stage (4 MMA K-steps)
 constexpr int A_PAD = 32;     // bytes added to A's 8-row stride (bank spread)
 constexpr long long WAIT_ITERS = 1LL << 22;
 
@@ -95,15 +96,17 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
     const int N = op.N;
     const int *rec = op.rec + b * DENSE_REC;
     const int s = rec[0], nb = rec[1], npad = rec[2], kpad = rec[3], wlo = rec[4], boff = rec[5];
-    const uint32_t sboA = (uint32_t)(kpad / 4) * 128u + A_PAD, sboB = (uint32_t)(kpad / 4) * 128u;
-    const uint32_t abytes = 16u * sboA, bbytes = (uint32_t)npad * kpad * 4u;
-    unsigned char *Ahi = smraw, *Alo = smraw + abytes;
-    unsigned char *Bhi = smraw + 2 * abytes, *Blo = Bhi + bbytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(Blo + bbytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    // per stage: A chunk (128 x KC, hi and lo) and B chunk (npad x KC, hi and lo)
+    constexpr uint32_t SBO_A = (KC / 4) * 128u + A_PAD, SBO_B = (KC / 4) * 128u;
+    constexpr uint32_t ABYTES = 16u * SBO_A;
+    const uint32_t bbytes = (uint32_t)npad * KC * 4u;
+    const uint32_t stage_bytes = 2u * ABYTES + 2u * bbytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smraw + 2u * stage_bytes);  // one per stage
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5;
     int ncols = 32;
     while (ncols < npad) ncols <<= 1;
+    const int nchunk = kpad / KC + (kpad % KC ? 1 : 0);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -112,20 +115,14 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    // B = D_b^T hi/lo, already in the canonical layout
-    {
-        const float4 *gh = reinterpret_cast<const float4 *>(op.hi + boff);
-        const float4 *gl = reinterpret_cast<const float4 *>(op.lo + boff);
-        float4 *sh = reinterpret_cast<float4 *>(Bhi), *sl = reinterpret_cast<float4 *>(Blo);
-        const int n4 = npad * kpad / 4;
-        for (int i = tid; i < n4; i += GM) {
-            sh[i] = gh[i];
-            sl[i] = gl[i];
-        }
-    }
-    // A = the 128 lines' windows, split into TF32 hi/lo
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
     const long long srow = AXIS == 0 ? 1 : (AXIS == 1 ? (long long)nx : (long long)nx * ny);
     const long long sa = AXIS == 0 ? (long long)nx : 1;
     const long long sc = AXIS == 2 ? (long long)nx : (long long)nx * ny;
@@ -133,77 +130,115 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
     // Every row of D_b sums to zero (the operator annihilates constants), so
     // each line's window is shifted by its value at the sub-domain start before
     // the split: the same result, with less cancellation in the contraction.
-    if (AXIS == 0) {
-        // rows are contiguous: consecutive threads read consecutive points of a line
-        const int tot = GM * kpad;
-        for (int q = tid; q < tot; q += GM) {
-            const int m = q / kpad, k = q % kpad;
-            const int pos = wlo + k;
-            const float c0 = m < nl ? f[gbase + (long long)m * sa + s] : 0.0f;
-            const float v = (m < nl && pos < N) ? f[gbase + (long long)m * sa + pos] - c0 : 0.0f;
-            const float h = tf32_part(v), l = tf32_part(v - h);
-            const uint32_t o = (uint32_t)(m >> 3) * sboA + (uint32_t)(k >> 2) * 128u + (m & 7) * 16u + (k & 3) * 4u;
-            *reinterpret_cast<float *>(Ahi + o) = h;
-            *reinterpret_cast<float *>(Alo + o) = l;
+    float c0 = 0.0f;
+    if (AXIS != 0 && tid < nl) c0 = f[gbase + (long long)s * srow + tid];
+    const uint32_t idesc = idesc_tf32(npad);
+    bool ok = true;
+    for (int c = 0; c < nchunk; ++c) {
+        const int st = c & 1;
+        unsigned char *Ahi = smraw + st * stage_bytes, *Alo = Ahi + ABYTES;
+        unsigned char *Bhi = Alo + ABYTES, *Blo = Bhi + bbytes;
+        // the MMAs of chunk c - 2 read this stage: wait for their commit
+        if (c >= 2) {
+            bool done = false;
+            for (long long it = 0; it < WAIT_ITERS && !done; ++it)
+                done = mbar_try_wait(smem_u32(mbar + st), (uint32_t)(((c - 2) >> 1) & 1));
+            ok = ok && done;
         }
-    } else {
-        // thread m owns line a0 + m; a warp's loads of one position are coalesced
-        const int m = tid;
-        const float c0 = m < nl ? f[gbase + (long long)s * srow + m] : 0.0f;
-        for (int k4 = 0; k4 < kpad; k4 += 4) {
-            float v[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int pos = wlo + k4 + t;
-                v[t] = (m < nl && pos < N) ? f[gbase + (long long)pos * srow + m] - c0 : 0.0f;
+        const int k0 = c * KC;
+        // B chunk: core matrices k0/4 .. k0/4 + KC/4 of every 8-row group
+        {
+            const int ncm = KC / 4;  // core matrices per group in a chunk
+            const int nq = (npad / 8) * ncm * 8;  // float4 per part
+            for (int i = tid; i < nq; i += GM) {
+                const int g = i / (ncm * 8), rem = i % (ncm * 8), cm = rem / 8, row = rem % 8;
+                const int kc = k0 / 4 + cm;
+                float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+                if (kc < kpad / 4) {
+                    const size_t go = (size_t)boff + (size_t)g * (kpad / 4) * 32 + (size_t)kc * 32 + row * 4;
+                    h = *reinterpret_cast<const float4 *>(op.hi + go);
+                    l = *reinterpret_cast<const float4 *>(op.lo + go);
+                }
+                const uint32_t so = (uint32_t)g * SBO_B + (uint32_t)cm * 128u + row * 16u;
+                *reinterpret_cast<float4 *>(Bhi + so) = h;
+                *reinterpret_cast<float4 *>(Blo + so) = l;
             }
-            float4 h, l;
-            h.x = tf32_part(v[0]);
-            h.y = tf32_part(v[1]);
-            h.z = tf32_part(v[2]);
-            h.w = tf32_part(v[3]);
-            l.x = tf32_part(v[0] - h.x);
-            l.y = tf32_part(v[1] - h.y);
-            l.z = tf32_part(v[2] - h.z);
-            l.w = tf32_part(v[3] - h.w);
-            const uint32_t o = (uint32_t)(m >> 3) * sboA + (uint32_t)(k4 >> 2) * 128u + (m & 7) * 16u;
-            *reinterpret_cast<float4 *>(Ahi + o) = h;
-            *reinterpret_cast<float4 *>(Alo + o) = l;
+        }
+        // A chunk: the lines' window points k0 .. k0 + KC - 1, split into TF32 hi/lo
+        if (AXIS == 0) {
+            for (int q = tid; q < GM * KC; q += GM) {
+                const int m = q / KC, k = q % KC;
+                const int pos = wlo + k0 + k;
+                float v = 0.0f;
+                if (m < nl && pos < N && k0 + k < kpad)
+                    v = f[gbase + (long long)m * sa + pos] - f[gbase + (long long)m * sa + s];
+                const float h = tf32_part(v), l = tf32_part(v - h);
+                const uint32_t o = (uint32_t)(m >> 3) * SBO_A + (uint32_t)(k >> 2) * 128u + (m & 7) * 16u + (k & 3) * 4u;
+                *reinterpret_cast<float *>(Ahi + o) = h;
+                *reinterpret_cast<float *>(Alo + o) = l;
+            }
+        } else {
+            const int m = tid;
+#pragma unroll 2
+            for (int k4 = 0; k4 < KC; k4 += 4) {
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int pos = wlo + k0 + k4 + t;
+                    v[t] = (m < nl && pos < N && k0 + k4 + t < kpad) ? f[gbase + (long long)pos * srow + m] - c0 : 0.0f;
+                }
+                float4 h, l;
+                h.x = tf32_part(v[0]);
+                h.y = tf32_part(v[1]);
+                h.z = tf32_part(v[2]);
+                h.w = tf32_part(v[3]);
+                l.x = tf32_part(v[0] - h.x);
+                l.y = tf32_part(v[1] - h.y);
+                l.z = tf32_part(v[2] - h.z);
+                l.w = tf32_part(v[3] - h.w);
+                const uint32_t o = (uint32_t)(m >> 3) * SBO_A + (uint32_t)(k4 >> 2) * 128u + (m & 7) * 16u;
+                *reinterpret_cast<float4 *>(Ahi + o) = h;
+                *reinterpret_cast<float4 *>(Alo + o) = l;
+            }
+        }
+        // generic-proxy shared stores -> visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+            const int ksteps = min(KC, kpad - k0) / 8;
+            for (int kk = 0; kk < ksteps; ++kk) {
+                const uint32_t ko = (uint32_t)kk * 256u;  // two 128-byte core matrices along K
+                const uint64_t dah = smem_desc(ah + ko, 128u, SBO_A), dal = smem_desc(al + ko, 128u, SBO_A);
+                const uint64_t dbh = smem_desc(bh + ko, 128u, SBO_B), dbl = smem_desc(bl + ko, 128u, SBO_B);
+                mma_tf32(tmem, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, idesc, 1u);
+                mma_tf32(tmem, dal, dbh, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mbar + st))
+                         : "memory");
         }
     }
-    // generic-proxy shared stores -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-    if (tid == 0) {
-        const uint32_t idesc = idesc_tf32(npad);
-        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-        for (int kk = 0; kk < kpad / 8; ++kk) {
-            const uint32_t ko = (uint32_t)kk * 256u;  // two 128-byte core matrices along K
-            const uint64_t dah = smem_desc(ah + ko, 128u, sboA), dal = smem_desc(al + ko, 128u, sboA);
-            const uint64_t dbh = smem_desc(bh + ko, 128u, sboB), dbl = smem_desc(bl + ko, 128u, sboB);
-            mma_tf32(tmem, dah, dbh, idesc, kk > 0 ? 1u : 0u);
-            mma_tf32(tmem, dah, dbl, idesc, 1u);
-            mma_tf32(tmem, dal, dbh, idesc, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(mbar))
-                     : "memory");
+    // the last commit covers every MMA issued before it
+    {
+        const int c = nchunk - 1;
+        bool done = false;
+        for (long long it = 0; it < WAIT_ITERS && !done; ++it)
+            done = mbar_try_wait(smem_u32(mbar + (c & 1)), (uint32_t)((c >> 1) & 1));
+        ok = ok && done;
     }
-    // bounded wait for the MMAs
-    bool done = false;
-    for (long long it = 0; it < WAIT_ITERS && !done; ++it) done = mbar_try_wait(smem_u32(mbar), 0u);
-    const int ok = __syncthreads_and(done ? 1 : 0);
+    const int all_ok = __syncthreads_and(ok ? 1 : 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    if (all_ok) {
         // accumulator lanes 32*warp .. +31 = lines; columns = outputs
         const long long obase = gbase + (long long)s * srow;
         const int m = tid;
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        for (int cb = 0; cb < npad; cb += 16) {
             uint32_t r[16];
-            const uint32_t ta_ = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t ta_ = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                 "[%16];"
@@ -215,7 +250,7 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
             if (m < nl) {
 #pragma unroll
                 for (int t = 0; t < 16; ++t) {
-                    const int n = c0 + t;
+                    const int n = cb + t;
                     if (n < nb) out[obase + (long long)n * srow + (long long)m * sa] = __uint_as_float(r[t]) * scale;
                 }
             }
@@ -231,8 +266,10 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
 
 size_t gemm_smem_bytes(int npad, int kpad)
 {
-    const size_t sboA = (size_t)(kpad / 4) * 128 + A_PAD;
-    return 2 * 16 * sboA + 2 * (size_t)npad * kpad * 4 + 16;
+    (void)kpad;
+    const size_t abytes = 16 * ((size_t)(KC / 4) * 128 + A_PAD);
+    const size_t stage = 2 * abytes + 2 * (size_t)npad * KC * 4;
+    return 2 * stage + 32;
 }
 
 template <int AXIS>

@@ -63,6 +63,8 @@ struct nopcs_ctx {
     std::vector<BoxRes> boxes;
     std::string err;
     cudaGraphExec_t step_exec = nullptr;
+    std::vector<cudaStream_t> branch;  // one capture branch per box
+    std::vector<cudaEvent_t> branch_ev;
     int *dev_err = nullptr;  // set by kernels whose bounded waits gave up
     bool profiling = false;
     std::vector<ProfPair> pool;
@@ -512,6 +514,8 @@ void nopcs_destroy(nopcs_ctx *ctx)
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    for (auto st : ctx->branch) cudaStreamDestroy(st);
+    for (auto ev : ctx->branch_ev) cudaEventDestroy(ev);
     for (auto &p : ctx->pool) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -618,13 +622,30 @@ nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps)
     if (nsteps < 0) return fail(ctx, NOPCS_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return NOPCS_OK;
     if (!ctx->profiling && !ctx->step_exec) {
-        // capture one step of every box once; replayed for every later step
+        // capture one step of every box once, replayed for every later step;
+        // each box's stage chain is its own branch of the graph (the boxes are
+        // independent), so the GPU runs small boxes side by side
+        const int nb = (int)ctx->boxes.size();
+        if ((int)ctx->branch.size() < nb) {
+            while ((int)ctx->branch.size() < nb) {
+                cudaStream_t st;
+                CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "graph branches");
+                ctx->branch.push_back(st);
+            }
+            while ((int)ctx->branch_ev.size() < nb + 1) {
+                cudaEvent_t ev;
+                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "graph branches");
+                ctx->branch_ev.push_back(ev);
+            }
+        }
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-        cudaError_t e = cudaSuccess;
-        for (auto &b : ctx->boxes) {
-            e = enqueue_step(ctx, b, ctx->cap_stream);
-            if (e != cudaSuccess) break;
+        cudaError_t e = cudaEventRecord(ctx->branch_ev[nb], ctx->cap_stream);
+        for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+            e = cudaStreamWaitEvent(ctx->branch[i], ctx->branch_ev[nb], 0);
+            if (e == cudaSuccess) e = enqueue_step(ctx, ctx->boxes[i], ctx->branch[i]);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->branch_ev[i], ctx->branch[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap_stream, ctx->branch_ev[i], 0);
         }
         cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (e != cudaSuccess) {

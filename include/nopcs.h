@@ -55,10 +55,12 @@ typedef enum {
 } nopcs_precision;
 
 typedef enum {
-    NOPCS_FORM_AUTO = 0,   /* library picks the solve form per box              */
+    NOPCS_FORM_AUTO = 0,   /* per box and axis, the faster of the two for FP32  */
+                           /* derivatives, measured at nopcs_init               */
     NOPCS_FORM_THOMAS = 1, /* per-sub-domain Thomas sweeps                      */
-    NOPCS_FORM_GEMM_3XTF32 = 2,
-    NOPCS_FORM_GEMM_BF16X3 = 3
+    NOPCS_FORM_GEMM_3XTF32 = 2, /* FP32 derivatives on the tensor cores (tcgen05, */
+                                /* split TF32); FP64 ones keep the Thomas form    */
+    NOPCS_FORM_GEMM_BF16X3 = 3  /* declared; returns NOPCS_EUNSUPPORTED          */
 } nopcs_form;
 
 /*
@@ -74,7 +76,8 @@ typedef struct {
     int gravity_axis;      /* 0, 1 or 2: gravity points along -axis; the interface  */
                            /* is the mid-plane normal to it                          */
     int sub_n[3];          /* NOHAP sub-domain length per axis (>= 3); 0 or >= n:   */
-                           /* one sub-domain                                         */
+                           /* one sub-domain; -1: the autotuner picks 32, 64 or 128 */
+                           /* by timing this GPU at nopcs_init                      */
     double Re, M, Pr, gamma;
     double suth_S;         /* Sutherland constant / T_s                             */
     double mub_scale;      /* factor on the bulk-viscosity law, Eq. reg             */
@@ -201,6 +204,14 @@ nopcs_status nopcs_filter(nopcs_ctx *ctx, int box);
  * the state holds a non-finite value.
  */
 nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out);
+
+/*
+ * Choices in force for box `box` (caller arrays of 3 ints, either may be
+ * NULL): the sub-domain length per axis (the autotuner's pick where the
+ * descriptor asked for -1) and the form of the FP32 derivative per axis
+ * (NOPCS_FORM_THOMAS or NOPCS_FORM_GEMM_3XTF32).
+ */
+nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form);
 
 /* Wait for all work enqueued on the context stream. */
 nopcs_status nopcs_synchronize(nopcs_ctx *ctx);

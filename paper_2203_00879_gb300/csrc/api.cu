@@ -4,6 +4,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <functional>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +33,8 @@ struct BoxRes {
     BoxDev dev{};
     LineOpBuf dop64[3], dop32[3], fop[3];
     GemmOpBuf gop[3];  // dense blocks of the FP32 derivative (tensor-core form)
+    int sub_n[3] = {0, 0, 0};     // sub-domain length in use per axis (tuned if asked)
+    bool deriv_gemm[3] = {false, false, false};  // FP32 derivative on the tensor cores
     bool mixed = false;
     double *Q = nullptr;
     void *W = nullptr, *R = nullptr;
@@ -106,8 +111,8 @@ bool valid_box(const nopcs_box_desc &d, std::string &m)
             m = "box lengths must be positive";
             return false;
         }
-        if (d.sub_n[a] < 0 || (d.sub_n[a] > 0 && d.sub_n[a] < 3)) {
-            m = "sub_n must be 0 or >= 3";
+        if (d.sub_n[a] < -1 || (d.sub_n[a] > 0 && d.sub_n[a] < 3)) {
+            m = "sub_n must be -1 (tune), 0 or >= 3";
             return false;
         }
     }
@@ -165,11 +170,135 @@ void free_box(BoxRes &b)
     b.partial = b.diag_out = nullptr;
 }
 
+// operator tables of one axis for the box's current sub-domain length
+nopcs_status build_axis_ops(nopcs_ctx *ctx, BoxRes &b, int a)
+{
+    const nopcs_box_desc &d = b.d;
+    std::string msg;
+    const int sn = b.sub_n[a];
+    if (!build_line_op(d.n[a], sn, KIND_DERIV, 0.0, 1e-16, b.dop64[a].host, msg) ||
+        !build_line_op(d.n[a], sn, KIND_DERIV, 0.0, 1e-8, b.dop32[a].host, msg) ||
+        !build_line_op(d.n[a], sn, KIND_FILTER, d.filter_alpha, 1e-16, b.fop[a].host, msg))
+        return fail(ctx, NOPCS_EINVAL, msg);
+    CK(b.dop64[a].upload(), "operator upload");
+    CK(b.dop32[a].upload(), "operator upload");
+    CK(b.fop[a].upload(), "operator upload");
+    if (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO) {
+        build_dense_blocks(b.dop32[a].host, b.gop[a].host);
+        if (gemm_smem_fits(b.gop[a].host)) {
+            CK(b.gop[a].upload(), "dense operator upload");
+        } else {
+            b.gop[a].release();
+            if (ctx->form == NOPCS_FORM_GEMM_3XTF32)
+                return fail(ctx, NOPCS_EUNSUPPORTED, "the tensor-core form needs sub-domains of at most 240 points");
+        }
+    }
+    return NOPCS_OK;
+}
+
 // mixed form: primitives W0 and base deviation Dn of the FP64 state Qn
 cudaError_t refresh_mixed(BoxRes &b, cudaStream_t st)
 {
     if (!b.mixed) return cudaSuccess;
     return launch_prep<float>(b.dev, b.Qn(), b.Wm(0), b.Dn(), st);
+}
+
+// ---- autotuner ---------------------------------------------------------------
+// For axes with sub_n = -1 the sub-domain length is chosen among 32, 64 and 128
+// by timing the flux sweep the RK path uses (the context precision) on this
+// GPU; under NOPCS_FORM_AUTO each axis's FP32 derivative takes the Thomas or
+// the tensor-core form, whichever measured faster.  Times come from CUDA
+// events on the context stream (one warm-up, three timed launches); choices
+// are cached per box shape for the process.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+float time_launches(cudaStream_t st, const std::function<cudaError_t()> &fn, cudaError_t &err)
+{
+    cudaEvent_t e0, e1;
+    err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) return 1e30f;
+    err = fn();
+    if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+    for (int i = 0; i < 3 && err == cudaSuccess; ++i) err = fn();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 1e30f;
+    if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
+{
+    cudaStream_t st = ctx->stream;
+    const BoxDev &x = b.dev;
+    char key0[96];
+    snprintf(key0, sizeof(key0), "%d,%d,%d,%d", x.n[0], x.n[1], x.n[2], b.mixed ? 1 : 0);
+    // primitives of the current state feed the timed sweeps
+    if (!b.mixed) CK(launch_prep<double>(x, b.Qn(), (double *)b.W, nullptr, st), "autotune");
+    for (int a = 0; a < 3; ++a) {
+        if (b.d.sub_n[a] != -1) continue;
+        const std::string key = std::string(key0) + ",s" + std::to_string(a);
+        int best = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) best = it->second;
+        }
+        if (best < 0) {
+            float tbest = 1e30f;
+            for (int cand : {32, 64, 128}) {
+                if (cand >= x.n[a] && cand != 32) continue;
+                b.sub_n[a] = cand;
+                nopcs_status s2 = build_axis_ops(ctx, b, a);
+                if (s2 != NOPCS_OK) return s2;
+                cudaError_t e;
+                float ms = b.mixed ? time_launches(st, [&] { return launch_line_flux<float>(b.dop32[a].dev, a, x, b.Wm(0), b.Rm(), 1, st); }, e)
+                                   : time_launches(st, [&] { return launch_line_flux<double>(b.dop64[a].dev, a, x, (double *)b.W, (double *)b.R, 1, st); }, e);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+                if (ms < tbest) {
+                    tbest = ms;
+                    best = cand;
+                }
+            }
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = best;
+        }
+        b.sub_n[a] = best;
+        nopcs_status s2 = build_axis_ops(ctx, b, a);
+        if (s2 != NOPCS_OK) return s2;
+    }
+    if (ctx->form == NOPCS_FORM_AUTO) {
+        // scratch FP32 fields inside the right-hand-side buffer (>= 2 np floats)
+        float *fin = (float *)b.R, *fout = fin + x.np;
+        CK(cudaMemsetAsync(fin, 0, 2 * (size_t)x.np * sizeof(float), st), "autotune");
+        for (int a = 0; a < 3; ++a) {
+            b.deriv_gemm[a] = false;
+            if (!b.gop[a].mem) continue;
+            const std::string key = std::string(key0) + ",g" + std::to_string(a) + "," + std::to_string(b.sub_n[a]);
+            int choice = -1;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune_cache.find(key);
+                if (it != g_tune_cache.end()) choice = it->second;
+            }
+            if (choice < 0) {
+                cudaError_t e1, e2;
+                const float tt = time_launches(st, [&] { return launch_line_field<float>(b.dop32[a].dev, a, x.n, fin, fout, 1.0, st); }, e1);
+                const float tg = time_launches(st, [&] { return launch_gemm_field(b.gop[a].dev, a, x.n, fin, fout, 1.0, ctx->dev_err, st); }, e2);
+                if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "autotune");
+                if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "autotune");
+                choice = tg < tt ? 1 : 0;
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune_cache[key] = choice;
+            }
+            b.deriv_gemm[a] = choice == 1;
+        }
+    }
+    return NOPCS_OK;
 }
 
 nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
@@ -196,19 +325,11 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     x.cE = 1.0 / (d.gamma * (d.gamma - 1.0) * d.M * d.M);
     x.dt = d.dt;
 
-    std::string msg;
     for (int a = 0; a < 3; ++a) {
-        if (!build_line_op(d.n[a], d.sub_n[a], KIND_DERIV, 0.0, 1e-16, b.dop64[a].host, msg) ||
-            !build_line_op(d.n[a], d.sub_n[a], KIND_DERIV, 0.0, 1e-8, b.dop32[a].host, msg) ||
-            !build_line_op(d.n[a], d.sub_n[a], KIND_FILTER, d.filter_alpha, 1e-16, b.fop[a].host, msg))
-            return fail(ctx, NOPCS_EINVAL, msg);
-        CK(b.dop64[a].upload(), "operator upload");
-        CK(b.dop32[a].upload(), "operator upload");
-        CK(b.fop[a].upload(), "operator upload");
-        if (ctx->form == NOPCS_FORM_GEMM_3XTF32) {
-            build_dense_blocks(b.dop32[a].host, b.gop[a].host);
-            CK(b.gop[a].upload(), "dense operator upload");
-        }
+        b.sub_n[a] = d.sub_n[a] == -1 ? 64 : d.sub_n[a];
+        b.deriv_gemm[a] = ctx->form == NOPCS_FORM_GEMM_3XTF32;
+        nopcs_status st = build_axis_ops(ctx, b, a);
+        if (st != NOPCS_OK) return st;
     }
     // base tables
     std::vector<double> rh, ph;
@@ -279,6 +400,11 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     b.diag_out = b.partial + (size_t)b.nblk_diag * 10;
     CK(launch_initial_state(x, d.seed, d.perturb_amp, b.Qn(), ctx->stream), "initial state");
     CK(refresh_mixed(b, ctx->stream), "initial state");
+    if (d.sub_n[0] == -1 || d.sub_n[1] == -1 || d.sub_n[2] == -1 || ctx->form == NOPCS_FORM_AUTO) {
+        nopcs_status st = autotune_box(ctx, b);
+        if (st != NOPCS_OK) return st;
+        CK(refresh_mixed(b, ctx->stream), "initial state");
+    }
     b.step = 0;
     return NOPCS_OK;
 }
@@ -474,12 +600,13 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
         return fail(nullptr, NOPCS_EUNSUPPORTED, "the BF16x3 tensor-core form is not built in this version");
     nopcs_ctx *ctx = new nopcs_ctx();
     ctx->prec = prec;
-    ctx->form = form == NOPCS_FORM_GEMM_3XTF32 ? NOPCS_FORM_GEMM_3XTF32 : NOPCS_FORM_THOMAS;
+    ctx->form = form;
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
     if (e == cudaSuccess) e = init_visc_kernels();
-    if (e == cudaSuccess && ctx->form == NOPCS_FORM_GEMM_3XTF32) e = init_gemm_kernels();
+    if (e == cudaSuccess && (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO))
+        e = init_gemm_kernels();
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->dev_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
@@ -595,7 +722,7 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
             }
         }
         cudaError_t e;
-        if (dtype == 1 && ctx->form == NOPCS_FORM_GEMM_3XTF32)
+        if (dtype == 1 && b.deriv_gemm[axis])
             e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)f, (float *)b.scratch, scale,
                                   ctx->dev_err, st);
         else if (dtype == 0)
@@ -606,7 +733,7 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
         src = b.scratch;
     }
     cudaError_t e;
-    if (dtype == 1 && ctx->form == NOPCS_FORM_GEMM_3XTF32)
+    if (dtype == 1 && b.deriv_gemm[axis])
         e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)src, (float *)df, scale, ctx->dev_err, st);
     else if (dtype == 0)
         e = launch_line_field<double>(op, axis, b.dev.n, (const double *)src, (double *)df, scale, st);
@@ -719,6 +846,18 @@ nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out)
     out->nonfinite = v[8] != 0.0;
     out->step = b.step;
     if (out->nonfinite) return fail(ctx, NOPCS_EUNSTABLE, "non-finite values in the state");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    const BoxRes &b = ctx->boxes[box];
+    for (int a = 0; a < 3; ++a) {
+        if (sub_n) sub_n[a] = b.sub_n[a];
+        if (deriv_form) deriv_form[a] = b.deriv_gemm[a] ? NOPCS_FORM_GEMM_3XTF32 : NOPCS_FORM_THOMAS;
+    }
     return NOPCS_OK;
 }
 

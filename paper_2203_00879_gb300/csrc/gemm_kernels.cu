@@ -289,6 +289,11 @@ cudaError_t launch_gemm_axis(const GemmOpDev &op, const int n[3], const float *f
 
 }  // namespace
 
+bool gemm_smem_fits(const DenseHost &h)
+{
+    return h.max_npad <= 256 && gemm_smem_bytes(h.max_npad, h.max_kpad) <= 227 * 1024;
+}
+
 cudaError_t init_gemm_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(gemm_deriv_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

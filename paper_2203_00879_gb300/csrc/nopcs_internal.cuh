@@ -90,6 +90,7 @@ struct GemmOpBuf {
     void release();
 };
 cudaError_t init_gemm_kernels();
+bool gemm_smem_fits(const DenseHost &h);
 // FP32 field derivative by the 3xTF32 tensor-core form; err <- 1 if a bounded
 // wait for the tensor cores gave up.
 cudaError_t launch_gemm_field(const GemmOpDev &op, int axis, const int n[3], const float *f, float *out,

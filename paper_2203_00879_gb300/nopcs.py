@@ -62,6 +62,7 @@ _L.nopcs_rhs.argtypes = [_vp, _i, _vp, _vp]
 _L.nopcs_filter.argtypes = [_vp, _i]
 _L.nopcs_diagnostics.argtypes = [_vp, _i, C.POINTER(nopcs_diag)]
 _L.nopcs_synchronize.argtypes = [_vp]
+_L.nopcs_box_info.argtypes = [_vp, _i, _vp, _vp]
 _L.nopcs_set_profiling.argtypes = [_vp, _i]
 _L.nopcs_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _i]
 _L.nopcs_kernel_name.argtypes = [_i]
@@ -72,7 +73,7 @@ _L.nopcs_operator_apply.argtypes = [_i, _i, _i, _d, _d, C.c_void_p, C.c_void_p]
 for _name in ("nopcs_operator_apply", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
-              "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows"):
+              "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows", "nopcs_box_info"):
     getattr(_L, _name).restype = _i
 
 
@@ -159,6 +160,14 @@ def nopcs_diagnostics(ctx, box: int, allow_unstable: bool = False) -> dict:
         _check(ctx, st)
     return dict(mass=d.mass, momentum=list(d.momentum), energy_total=d.energy_total, max_speed=d.max_speed,
                 max_dp=d.max_dp, max_mach=d.max_mach, step=d.step, nonfinite=d.nonfinite)
+
+
+def nopcs_box_info(ctx, box: int) -> dict:
+    """Sub-domain length and FP32-derivative form in force per axis."""
+    sub = (_i * 3)()
+    form = (_i * 3)()
+    _check(ctx, _L.nopcs_box_info(ctx, box, sub, form))
+    return {"sub_n": list(sub), "deriv_form": list(form)}
 
 
 def nopcs_synchronize(ctx) -> None:

@@ -60,3 +60,38 @@ def test_gemm_form_fp64_fields_use_thomas():
         assert field_rel(out.cpu().numpy()[None], ref[None])[0] <= 1e-12
     finally:
         N.nopcs_destroy(ctx)
+
+
+def test_autotuner_choices_and_parity():
+    """sub_n = -1 and NOPCS_FORM_AUTO: the autotuner picks a sub-domain length
+    among 32/64/128 and a derivative form per axis; results still match the
+    oracle (NOHAP results do not depend on the split)."""
+    import torch
+    N = binding()
+    n = (160, 140, 130)
+    p = S.box_params(n, sub_n=(-1, -1, -1), perturb_amp=1e-4)
+    ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_AUTO, stream=stream_ptr())
+    try:
+        info = N.nopcs_box_info(ctx, 0)
+        assert all(sn in (32, 64, 128) for sn in info["sub_n"]), info
+        assert all(fm in (N.NOPCS_FORM_THOMAS, N.NOPCS_FORM_GEMM_3XTF32) for fm in info["deriv_form"]), info
+        f = S.sine_field(n, kmax=16, seed=5, noise=1e-3)
+        fd = to_dev(f, np.float32)
+        out = torch.empty_like(fd)
+        h = p["len"][0] / (n[0] - 1)
+        for axis in range(3):
+            N.nopcs_derivative(ctx, 0, axis, 1, 1, fd.data_ptr(), out.data_ptr(), stream_ptr())
+            N.nopcs_synchronize(ctx)
+            ref = oracle.deriv3d(fd.cpu().numpy().astype(np.float64), axis, h, info["sub_n"][axis])
+            assert field_rel(out.cpu().numpy()[None], ref[None])[0] <= 1e-5
+        print("autotuner", info)
+        # a few RK steps with the tuned sub-domains match the oracle
+        N.nopcs_rk_step(ctx, 3)
+        Q = torch.empty((5, n[2], n[1], n[0]), dtype=torch.float64, device="cuda")
+        N.nopcs_get_state(ctx, 0, Q.data_ptr())
+        pr = dict(p, sub_n=tuple(info["sub_n"]), base_subtract=1)
+        orc = oracle.Solver(pr)
+        ref = orc.step(orc.initial_state(), 3)
+        assert np.all(field_rel(Q.cpu().numpy(), ref) <= 1e-5)
+    finally:
+        N.nopcs_destroy(ctx)

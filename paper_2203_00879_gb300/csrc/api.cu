@@ -34,6 +34,7 @@ struct BoxRes {
     LineOpBuf dop64[3], dop32[3], fop[3];
     GemmOpBuf gop[3];  // dense blocks of the FP32 derivative (tensor-core form)
     int sub_n[3] = {0, 0, 0};     // sub-domain length in use per axis (tuned if asked)
+    int lines[3] = {0, 0, 0};     // flux-sweep lines per block per axis (0: default)
     bool deriv_gemm[3] = {false, false, false};  // FP32 derivative on the tensor cores
     bool mixed = false;
     double *Q = nullptr;
@@ -204,12 +205,14 @@ cudaError_t refresh_mixed(BoxRes &b, cudaStream_t st)
 }
 
 // ---- autotuner ---------------------------------------------------------------
-// For axes with sub_n = -1 the sub-domain length is chosen among 32, 64 and 128
-// by timing the flux sweep the RK path uses (the context precision) on this
-// GPU; under NOPCS_FORM_AUTO each axis's FP32 derivative takes the Thomas or
-// the tensor-core form, whichever measured faster.  Times come from CUDA
+// Per axis, the flux sweep's tile width (16 or 32 lines per block) and, where
+// the descriptor asks with sub_n = -1, the sub-domain length (32, 64 or 128)
+// are chosen by timing the sweep the RK path uses (the context precision) on
+// this GPU; under NOPCS_FORM_AUTO each axis's FP32 derivative takes the Thomas
+// or the tensor-core form, whichever measured faster.  Times come from CUDA
 // events on the context stream (one warm-up, three timed launches); choices
-// are cached per box shape for the process.
+// are cached per box shape for the process.  Boxes below 2^20 points keep the
+// defaults unless a sub-domain length is requested.
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune_cache;
 
@@ -240,9 +243,10 @@ nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
     // primitives of the current state feed the timed sweeps
     if (!b.mixed) CK(launch_prep<double>(x, b.Qn(), (double *)b.W, nullptr, st), "autotune");
     for (int a = 0; a < 3; ++a) {
-        if (b.d.sub_n[a] != -1) continue;
-        const std::string key = std::string(key0) + ",s" + std::to_string(a);
-        int best = -1;
+        const bool tune_sub = b.d.sub_n[a] == -1;
+        if (!tune_sub && x.np < (1LL << 20)) continue;
+        const std::string key = std::string(key0) + ",s" + std::to_string(a) + "," + std::to_string(b.d.sub_n[a]);
+        int best = -1;  // sub_n * 1000 + lines per block
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(key);
@@ -250,23 +254,35 @@ nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
         }
         if (best < 0) {
             float tbest = 1e30f;
-            for (int cand : {32, 64, 128}) {
-                if (cand >= x.n[a] && cand != 32) continue;
-                b.sub_n[a] = cand;
-                nopcs_status s2 = build_axis_ops(ctx, b, a);
-                if (s2 != NOPCS_OK) return s2;
-                cudaError_t e;
-                float ms = b.mixed ? time_launches(st, [&] { return launch_line_flux<float>(b.dop32[a].dev, a, x, b.Wm(0), b.Rm(), 1, st); }, e)
-                                   : time_launches(st, [&] { return launch_line_flux<double>(b.dop64[a].dev, a, x, (double *)b.W, (double *)b.R, 1, st); }, e);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
-                if (ms < tbest) {
-                    tbest = ms;
-                    best = cand;
+            std::vector<int> cands;
+            if (tune_sub)
+                cands = {32, 64, 128};
+            else
+                cands = {b.sub_n[a]};
+            for (int cand : cands) {
+                if (tune_sub && cand >= x.n[a] && cand != 32) continue;
+                if (tune_sub) {
+                    b.sub_n[a] = cand;
+                    nopcs_status s2 = build_axis_ops(ctx, b, a);
+                    if (s2 != NOPCS_OK) return s2;
+                }
+                for (int ln : {16, 32}) {
+                    cudaError_t e;
+                    float ms = b.mixed ? time_launches(st, [&] { return launch_line_flux<float>(b.dop32[a].dev, a, x, b.Wm(0), b.Rm(), 1, st, ln); }, e)
+                                       : time_launches(st, [&] { return launch_line_flux<double>(b.dop64[a].dev, a, x, (double *)b.W, (double *)b.R, 1, st, ln); }, e);
+                    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+                    if (ms < tbest) {
+                        tbest = ms;
+                        best = cand * 1000 + ln;
+                    }
                 }
             }
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune_cache[key] = best;
         }
+        b.lines[a] = best % 1000;
+        if (!tune_sub) continue;
+        best /= 1000;
         b.sub_n[a] = best;
         nopcs_status s2 = build_axis_ops(ctx, b, a);
         if (s2 != NOPCS_OK) return s2;
@@ -400,7 +416,8 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     b.diag_out = b.partial + (size_t)b.nblk_diag * 10;
     CK(launch_initial_state(x, d.seed, d.perturb_amp, b.Qn(), ctx->stream), "initial state");
     CK(refresh_mixed(b, ctx->stream), "initial state");
-    if (d.sub_n[0] == -1 || d.sub_n[1] == -1 || d.sub_n[2] == -1 || ctx->form == NOPCS_FORM_AUTO) {
+    if (d.sub_n[0] == -1 || d.sub_n[1] == -1 || d.sub_n[2] == -1 || ctx->form == NOPCS_FORM_AUTO ||
+        x.np >= (1LL << 20)) {
         nopcs_status st = autotune_box(ctx, b);
         if (st != NOPCS_OK) return st;
         CK(refresh_mixed(b, ctx->stream), "initial state");
@@ -453,7 +470,8 @@ cudaError_t enqueue_rhs_sweeps(nopcs_ctx *ctx, BoxRes &b, const T *W, T *R, cuda
     const bool f32 = sizeof(T) == 4;
     for (int a = 0; a < 3; ++a) {
         Timed t(ctx, st, K_SX + a);
-        cudaError_t e = launch_line_flux<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, b.dev, W, R, a == 0, st);
+        cudaError_t e =
+            launch_line_flux<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, b.dev, W, R, a == 0, st, b.lines[a]);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

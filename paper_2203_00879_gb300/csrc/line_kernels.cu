@@ -385,9 +385,13 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     // at least 256 threads: the extra ones only stage and store, which keeps
     // more loads in flight per SM
+    // extra threads beyond the lines x fields of the solve only stage and
+    // store, which keeps more loads in flight per SM
     int threads = a.lines * NF;
     threads = (threads + 31) / 32 * 32;
-    if (threads < 256) threads = 256;
+    if (threads < 8 * a.lines) threads = 8 * a.lines;
+    if (threads < 128) threads = 128;
+    if (threads > 1024) threads = (a.lines * NF + 31) / 32 * 32;
     if (threads > 1024) return cudaErrorInvalidConfiguration;
     line_kernel<T, MODE, AXIS><<<(unsigned)nblk, threads, smem, st>>>(op, a);
     return cudaGetLastError();
@@ -443,7 +447,7 @@ cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], con
 
 template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
-                             int first, cudaStream_t st)
+                             int first, cudaStream_t st, int lines)
 {
     LineArgs<T> a{};
     for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
@@ -460,7 +464,7 @@ cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, co
         a.b0 = (const T *)bx.rho_b32;
         a.b1 = (const T *)bx.H_b32;
     }
-    return launch_any<T, MODE_FLUX>(op, axis, a, sizeof(T) == 4 ? 32 : 16, st);
+    return launch_any<T, MODE_FLUX>(op, axis, a, lines > 0 ? lines : (sizeof(T) == 4 ? 32 : 16), st);
 }
 
 cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
@@ -485,8 +489,8 @@ template cudaError_t launch_line_field<float>(const LineOpDev &, int, const int 
 template cudaError_t launch_line_field<double>(const LineOpDev &, int, const int *, const double *,
                                                double *, double, cudaStream_t);
 template cudaError_t launch_line_flux<float>(const LineOpDev &, int, const BoxDev &, const float *, float *,
-                                             int, cudaStream_t);
+                                             int, cudaStream_t, int);
 template cudaError_t launch_line_flux<double>(const LineOpDev &, int, const BoxDev &, const double *,
-                                              double *, int, cudaStream_t);
+                                              double *, int, cudaStream_t, int);
 
 }  // namespace nopcs

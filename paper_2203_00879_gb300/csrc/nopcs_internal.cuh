@@ -129,9 +129,10 @@ template <typename T>
 cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], const T *f, T *out,
                               double scale, cudaStream_t st);
 // FLUX: R (= or -=) L(flux_axis(W)) / h.  first != 0 stores, else subtracts.
+// lines: lines per block (tile width; 0 = default for the precision).
 template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
-                             int first, cudaStream_t st);
+                             int first, cudaStream_t st, int lines = 0);
 // FILTER (FP64): Qout = L(Q - base) + base, 5 fields.
 cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
                                const double *Qin, double *Qout, cudaStream_t st);

@@ -19,7 +19,7 @@ TOL2 = {0: 1e-12, 1: 5e-5}
 
 def _ctx(N, n, sub_n):
     p = S.box_params(n, sub_n=sub_n, perturb_amp=0.0)
-    return N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=stream_ptr()), p
+    return N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_THOMAS, stream=stream_ptr()), p
 
 
 def _oracle(f, axis, h, sub_n, order):

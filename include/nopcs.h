@@ -71,7 +71,8 @@ typedef enum {
  * by T_s.
  */
 typedef struct {
-    int n[3];              /* grid points per axis, >= 5; nodes lie on the walls    */
+    int n[3];              /* grid points per axis, >= 5, product < 2^31; nodes    */
+                           /* lie on the walls                                      */
     double len[3];         /* box lengths; spacing h = len / (n - 1)                */
     int gravity_axis;      /* 0, 1 or 2: gravity points along -axis; the interface  */
                            /* is the mid-plane normal to it                          */

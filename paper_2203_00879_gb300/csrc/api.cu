@@ -117,6 +117,10 @@ bool valid_box(const nopcs_box_desc &d, std::string &m)
             return false;
         }
     }
+    if ((long long)d.n[0] * d.n[1] * d.n[2] >= (1LL << 31)) {
+        m = "a box holds fewer than 2^31 points (kernels index a field with 32 bits)";
+        return false;
+    }
     if (d.gravity_axis < 0 || d.gravity_axis > 2) {
         m = "gravity_axis must be 0, 1 or 2";
         return false;

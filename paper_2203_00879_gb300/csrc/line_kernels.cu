@@ -25,12 +25,13 @@ namespace nopcs {
 template <typename T>
 struct LineArgs {
     int n[3];
-    long long np;
     int lines;      // lines per block (LINES)
     int ntile_a;    // tiles along the line-tile axis
     int rt;         // row capacity of a field column (op.max_tile)
-    const T *in;    // FIELD: f; FLUX: W (6 fields); FILTER: Q (5 fields)
-    T *out;         // FIELD: df; FLUX: R (5 fields); FILTER: Qout (5 fields)
+    // one base pointer per field, so a node is one 32-bit index away from a
+    // kernel parameter (fields hold < 2^31 points)
+    const T *in[6]; // FIELD: f; FLUX: W (6 fields); FILTER: Q (5 fields)
+    T *out[5];      // FIELD: df; FLUX: R (5 fields); FILTER: Qout (5 fields)
     T scale;        // 1/h for FIELD and FLUX
     int first;      // FLUX: store (1) or subtract (0)
     int ga;         // gravity axis
@@ -96,7 +97,6 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     T *tiv = tcp + KC;
     T *sm = tiv + KC;
     const int nx = a.n[0], ny = a.n[1];
-    const long long np = a.np;
 
     const int b = blockIdx.x % op.nsub;
     const int tile = blockIdx.x / op.nsub;
@@ -111,10 +111,10 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     const int j0s = rec[4], lens = rec[5], j0e = rec[7], lene = rec[8];
     const int lo = rec[10], hi = rec[11];
     const int nrows = thi - tlo + 1;
-    const long long srow = AXIS == 0 ? 1 : (AXIS == 1 ? (long long)nx : (long long)nx * ny);
-    const long long sa = AXIS == 0 ? (long long)nx : 1;
-    const long long sc = AXIS == 2 ? (long long)nx : (long long)nx * ny;
-    const long long gbase = (long long)cc * sc + (long long)a0 * sa + (long long)tlo * srow;
+    const int srow = AXIS == 0 ? 1 : (AXIS == 1 ? nx : nx * ny);
+    const int sa = AXIS == 0 ? nx : 1;
+    const int sc = AXIS == 2 ? nx : nx * ny;
+    const int gbase = cc * sc + a0 * sa + tlo * srow;
     // which of (row, line, cc) is the coordinate along the gravity axis
     const int gsel = a.ga == AXIS ? 0 : (a.ga == (AXIS == 0 ? 1 : 0) ? 1 : 2);
     const size_t fs = (size_t)RT * LP;
@@ -148,7 +148,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             rstep = blockDim.x / LINES;
         }
         for (int l = l0; l < nl; l += lstep) {
-            const T *src = a.in + gbase + (long long)l * sa;
+            const int src = gbase + l * sa;
             T *dst = sm + l;
             const int gl = gsel == 1 ? a0 + l : cc;
             for (int r = r0; r < nrows; r += U * rstep) {
@@ -157,9 +157,9 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                 for (int u = 0; u < U; ++u) {
                     const int rr = r + u * rstep;
                     if (rr < nrows) {
-                        const T *p = src + (long long)rr * srow;
+                        const int p = src + rr * srow;
 #pragma unroll
-                        for (int k = 0; k < NIN; ++k) v[u][k] = p[k * np];
+                        for (int k = 0; k < NIN; ++k) v[u][k] = a.in[k][p];
                     }
                 }
 #pragma unroll
@@ -312,9 +312,9 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             r0 = threadIdx.x / LINES;
             rstep = blockDim.x / LINES;
         }
-        const long long obase = gbase + (long long)(s - tlo) * srow;
+        const int obase = gbase + (s - tlo) * srow;
         for (int ll = l0; ll < nl; ll += lstep) {
-            T *dstg = a.out + obase + (long long)ll * sa;
+            const int dstg = obase + ll * sa;
             const T *srcs = sm + (size_t)(s - tlo) * LP + ll;
             const int gl = gsel == 1 ? a0 + ll : cc;
             for (int r = r0; r < nown; r += U * rstep) {
@@ -325,7 +325,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                         const int rr = r + u * rstep;
                         if (rr < nown) {
 #pragma unroll
-                            for (int f = 0; f < 5; ++f) old[u][f] = dstg[f * np + (long long)rr * srow];
+                            for (int f = 0; f < 5; ++f) old[u][f] = a.out[f][dstg + rr * srow];
                         }
                     }
                 }
@@ -334,22 +334,22 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                     const int rr = r + u * rstep;
                     if (rr >= nown) continue;
                     const T *src = srcs + (size_t)rr * LP;
-                    T *o = dstg + (long long)rr * srow;
+                    const int o = dstg + rr * srow;
                     if constexpr (MODE == MODE_FIELD) {
-                        o[0] = src[0] * a.scale;
+                        a.out[0][o] = src[0] * a.scale;
                     } else if constexpr (MODE == MODE_FLUX) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) {
                             const T v = -src[f * fs] * a.scale;
-                            o[f * np] = a.first ? v : old[u][f] + v;
+                            a.out[f][o] = a.first ? v : old[u][f] + v;
                         }
                     } else {
                         const int gk = gsel == 0 ? s + rr : gl;
-                        o[0] = src[0] + a.b0[gk];
-                        o[np] = src[fs];
-                        o[2 * np] = src[2 * fs];
-                        o[3 * np] = src[3 * fs];
-                        o[4 * np] = src[4 * fs] + a.b1[gk];
+                        a.out[0][o] = src[0] + a.b0[gk];
+                        a.out[1][o] = src[fs];
+                        a.out[2][o] = src[2 * fs];
+                        a.out[3][o] = src[3 * fs];
+                        a.out[4][o] = src[4 * fs] + a.b1[gk];
                     }
                 }
             }
@@ -438,9 +438,8 @@ cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], con
 {
     LineArgs<T> a{};
     for (int d = 0; d < 3; ++d) a.n[d] = n[d];
-    a.np = (long long)n[0] * n[1] * n[2];
-    a.in = f;
-    a.out = out;
+    a.in[0] = f;
+    a.out[0] = out;
     a.scale = (T)scale;
     return launch_any<T, MODE_FIELD>(op, axis, a, sizeof(T) == 4 ? 64 : 32, st);
 }
@@ -451,9 +450,8 @@ cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, co
 {
     LineArgs<T> a{};
     for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
-    a.np = bx.np;
-    a.in = W;
-    a.out = R;
+    for (int k = 0; k < 6; ++k) a.in[k] = W + (size_t)k * bx.np;
+    for (int k = 0; k < 5; ++k) a.out[k] = R + (size_t)k * bx.np;
     a.scale = (T)bx.inv_h[axis];
     a.first = first;
     a.ga = bx.ga;
@@ -472,9 +470,10 @@ cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, 
 {
     LineArgs<double> a{};
     for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
-    a.np = bx.np;
-    a.in = Qin;
-    a.out = Qout;
+    for (int k = 0; k < 5; ++k) {
+        a.in[k] = Qin + (size_t)k * bx.np;
+        a.out[k] = Qout + (size_t)k * bx.np;
+    }
     a.ga = bx.ga;
     // the base tables hold the hydrostatic state in the base-subtracted form
     // and zeros in the plain form

@@ -301,27 +301,34 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
 {
     __shared__ double sh[DIAG_REC][DIAG_THREADS];
     const long long np = bx.np;
+    const int nx = bx.n[0], ny = bx.n[1], rows = bx.n[1] * bx.n[2];
+    const double gm1 = bx.gamma - 1.0, igam = 1.0 / bx.gamma;
+    // maxima of |V|^2 and Mach^2 are kept and their square roots taken once
+    // in the final kernel (the square root is monotone); one FP64 division
+    // for 1/rho and one for Mach^2 = |V|^2 rho / (gamma p) per point
     double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
-         p += (long long)gridDim.x * blockDim.x) {
-        int c[3];
-        coords(bx, p, c);
-        const int kg = c[bx.ga];
-        const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
-        const bool bad = !isfinite(r) || !isfinite(mx) || !isfinite(my) || !isfinite(mz) || !isfinite(E);
-        if (bad) v[8] = 1.0;
-        v[0] += r;
-        v[1] += mx;
-        v[2] += my;
-        v[3] += mz;
-        v[4] += E + r * bx.g * (kg * bx.h[bx.ga]);
-        const double u = mx / r, vv = my / r, w = mz / r;
-        const double sp = sqrt(u * u + vv * vv + w * w);
-        const double pr = (bx.gamma - 1.0) * (E - 0.5 * r * sp * sp);
-        const double T = bx.gm2 * pr / r;
-        v[5] = fmax(v[5], sp);
-        v[6] = fmax(v[6], fabs(pr - bx.p_h64[kg]));
-        v[7] = fmax(v[7], sp * bx.M / sqrt(T));
+    for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+        const int y = rw % ny, z = rw / ny;
+        const long long base = (long long)rw * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long p = base + x;
+            const int kg = bx.ga == 0 ? x : (bx.ga == 1 ? y : z);
+            const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
+            const bool bad = !isfinite(r) || !isfinite(mx) || !isfinite(my) || !isfinite(mz) || !isfinite(E);
+            if (bad) v[8] = 1.0;
+            v[0] += r;
+            v[1] += mx;
+            v[2] += my;
+            v[3] += mz;
+            v[4] += E + r * bx.g * (kg * bx.h[bx.ga]);
+            const double ir = 1.0 / r;
+            const double u = mx * ir, vv = my * ir, w = mz * ir;
+            const double s2 = u * u + vv * vv + w * w;
+            const double pr = gm1 * (E - 0.5 * r * s2);
+            v[5] = fmax(v[5], s2);
+            v[6] = fmax(v[6], fabs(pr - bx.p_h64[kg]));
+            v[7] = fmax(v[7], s2 * r * igam / pr);
+        }
     }
     for (int k = 0; k < DIAG_REC; ++k) sh[k][threadIdx.x] = v[k];
     __syncthreads();
@@ -346,6 +353,8 @@ __global__ void diag_final_kernel(const BoxDev bx, const double *partial, int nb
     }
     const double dV = bx.h[0] * bx.h[1] * bx.h[2];
     for (int k = 0; k < 5; ++k) v[k] *= dV;
+    v[5] = sqrt(v[5]);
+    v[7] = sqrt(v[7]);
     for (int k = 0; k < DIAG_REC; ++k) out[k] = v[k];
 }
 
@@ -387,8 +396,8 @@ cudaError_t launch_initial_state(const BoxDev &bx, unsigned long long seed, doub
 
 int diag_blocks(long long np)
 {
-    long long b = (np + DIAG_THREADS - 1) / DIAG_THREADS;
-    return b > 1024 ? 1024 : (int)b;
+    (void)np;
+    return 152 * 8;  // grid-stride over (y, z) rows: 8 blocks per SM
 }
 
 cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partial, int nblk, double *out,

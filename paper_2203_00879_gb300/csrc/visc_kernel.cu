@@ -6,13 +6,13 @@
 // divergence of nodal viscous fluxes, and each nodal flux needs second-order
 // explicit gradients of u, v, w, T at its node: a +-2 stencil (+-3 next to a
 // wall, where both operators are one-sided).  A block owns a TX x TY column
-// tile and marches along z, keeping the primitives (u, v, w, T) of the seven
-// planes o-3 .. o+3 around the output plane o, with a two-node x/y halo, in a
+// tile and marches along z, keeping the primitives (u, v, w, T) of the five
+// planes o-2 .. o+2 around the output plane o, with a two-node x/y halo, in a
 // shared-memory ring; every primitive is loaded from global memory once per
 // block and plane.  For each plane the block then
 //   1. evaluates every nodal viscous flux once: E_v on the plane's tile plus
 //      a one-node x halo, F_v on the tile plus a one-node y halo, and G_v on
-//      the tile of the planes the z divergence needs, kept in a ring of four
+//      the tile of the planes the z divergence needs, kept in a ring of three
 //      planes so each G_v plane is computed once and used twice;
 //   2. takes the divergence at its tile nodes, adds the gravity source to the
 //      convective right-hand side accumulated by the sweeps, holds momentum at
@@ -32,24 +32,29 @@ namespace {
 
 constexpr int TX = 32, TY = 8, HALO = 2;
 constexpr int PX = TX + 2 * HALO, PY = TY + 2 * HALO, PLANE = PX * PY;
-constexpr int RING = 7;   // planes o-3 .. o+3
+constexpr int RING = 5;   // planes o-2 .. o+2 (o-3 .. o+1 / o-1 .. o+3 at a wall)
 constexpr int NPF = 4;    // u, v, w, T
-constexpr int GSLOTS = 4; // planes of G_v kept
+constexpr int GSLOTS = 3; // planes of G_v kept
 
+// Every field array is passed as its own base pointer, so a node's address is
+// one 32-bit index away from a kernel parameter (boxes hold < 2^31 points).
 template <typename T>
 struct VArgs {
     int n[3];
-    long long np;
+    int np;
     T ih2[3];             // 1 / (2 h)
     int ga, zc;           // gravity axis, planes per block
     T gm2, iRe, kq, S1, S, c0, c1, g;
-    const T *W;
+    const T *W[6];
     const T *rho_b, *p_b;                 // base tables (zeros in the plain form)
     const float *T_b, *ip_b, *ir_b;       // mixed form: T_b, 1/p_b, 1/rho_b
-    const T *R;
+    const T *R[5];
     int stage;
     double dt;
-    StageRegs<T> rg_out;
+    T *Rout[5];                           // stage 0: right-hand side out
+    double *Qn[5], *acc[5], *Qout[5];     // FP64 stage registers
+    float *Kacc[5], *Dn[5];               // mixed form: slope sum, deviation of Q_n
+    T *Wn[6];                             // mixed form: next stage's W
     const double *rho_b64, *E_b64;        // mixed form: base state for the deviation of Q_n
     float gm1;                            // gamma - 1
 };
@@ -63,43 +68,6 @@ struct Ring {
         return s[((z % RING) * NPF + f) * PLANE + (y - y0 + HALO) * PX + (x - x0 + HALO)];
     }
 };
-
-// temperature from W at (global index i, gravity coordinate kg)
-template <typename T>
-__device__ __forceinline__ T temp_of(const VArgs<T> &a, long long i, int kg)
-{
-    const T w0 = a.W[i], w4 = a.W[4 * a.np + i];
-    if constexpr (sizeof(T) == 4) {
-        // T = T_b (1 + p'/p_b) / (1 + rho'/rho_b): exact at rest, where p' = rho' = 0
-        const float rr = w0 * a.ir_b[kg];
-        return a.T_b[kg] + a.T_b[kg] * (w4 * a.ip_b[kg] - rr) / (1.0f + rr);
-    } else {
-        return a.gm2 * (a.p_b[kg] + w4) / (a.rho_b[kg] + w0);
-    }
-}
-
-template <typename T>
-__device__ void load_plane(const VArgs<T> &a, const Ring<T> &rg, int z)
-{
-    const int nx = a.n[0], ny = a.n[1];
-    for (int idx = threadIdx.x; idx < PLANE; idx += blockDim.x) {
-        const int lx = idx % PX, ly = idx / PX;
-        const int gx = rg.x0 - HALO + lx, gy = rg.y0 - HALO + ly;
-        T u = 0, v = 0, w = 0, t = 0;
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-            const long long i = gx + (long long)nx * (gy + (long long)ny * z);
-            u = a.W[a.np + i];
-            v = a.W[2 * a.np + i];
-            w = a.W[3 * a.np + i];
-            t = temp_of(a, i, a.ga == 0 ? gx : (a.ga == 1 ? gy : z));
-        }
-        T *p = rg.s + (size_t)(z % RING) * NPF * PLANE + idx;
-        p[0] = u;
-        p[PLANE] = v;
-        p[2 * PLANE] = w;
-        p[3 * PLANE] = t;
-    }
-}
 
 // A plane load split in two halves: issue() starts the global loads of this
 // thread's ring nodes into registers, finish() computes T and writes the ring,
@@ -128,16 +96,16 @@ struct PlaneLoad {
     __device__ __forceinline__ void issue(const VArgs<T> &a, int zz)
     {
         z = zz;
-        const long long zo = (long long)a.n[0] * a.n[1] * zz;
+        const int zo = a.n[0] * a.n[1] * zz;
 #pragma unroll
         for (int t = 0; t < PL_PER_THREAD; ++t) {
             if (goff[t] >= 0) {
-                const long long i = zo + goff[t];
-                w0[t] = a.W[i];
-                u[t] = a.W[a.np + i];
-                v[t] = a.W[2 * a.np + i];
-                w[t] = a.W[3 * a.np + i];
-                w4[t] = a.W[4 * a.np + i];
+                const int i = zo + goff[t];
+                w0[t] = a.W[0][i];
+                u[t] = a.W[1][i];
+                v[t] = a.W[2][i];
+                w[t] = a.W[3][i];
+                w4[t] = a.W[4][i];
             }
         }
     }
@@ -269,21 +237,19 @@ __device__ __forceinline__ void flux_z(const VArgs<T> &a, const Stencil<T, EDGE>
 }
 
 // primitives of a stage state from its FP32 deviation D = (rho', m_x, m_y, m_z, E')
-__device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, long long p, int kg, const float D[5])
+__device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, int p, int kg, const float D[5])
 {
-    const long long np = a.np;
     const float rho = a.rho_b[kg] + D[0];
     const float ir = __fdividef(1.0f, rho);
     const float u = D[1] * ir, v = D[2] * ir, w = D[3] * ir;
     const float ke = 0.5f * (D[1] * u + D[2] * v + D[3] * w);
     const float pd = a.gm1 * (D[4] - ke);
-    float *Wn = a.rg_out.Wn;
-    Wn[p] = D[0];
-    Wn[np + p] = u;
-    Wn[2 * np + p] = v;
-    Wn[3 * np + p] = w;
-    Wn[4 * np + p] = pd;
-    Wn[5 * np + p] = D[4] + pd;
+    a.Wn[0][p] = D[0];
+    a.Wn[1][p] = u;
+    a.Wn[2][p] = v;
+    a.Wn[3][p] = w;
+    a.Wn[4][p] = pd;
+    a.Wn[5][p] = D[4] + pd;
 }
 
 // Mixed form of the classical RK4 stage.  The slopes are FP32 (they are FP32
@@ -291,10 +257,9 @@ __device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, long long p
 // to the FP64 state once, Q_n += dt/6 K, in FP64.  The stage states
 // Q_n + c dt k are formed as FP32 deviations from the hydrostatic base, the
 // same quantities the primitive recovery of the FP64 form rounds to FP32.
-__device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p, int kg, const float r[5],
+__device__ __forceinline__ void mixed_update(const VArgs<float> &a, int p, int kg, const float r[5],
                                              const float kold[5], const float dn[5])
 {
-    const long long np = a.np;
     const int s = a.stage;
     float K[5];
     if (s == 1) {
@@ -308,7 +273,7 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p,
     float D[5];
     if (s < 4) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) a.rg_out.Kacc[k * np + p] = K[k];
+        for (int k = 0; k < 5; ++k) a.Kacc[k][p] = K[k];
         const float c = (float)(s == 3 ? a.dt : 0.5 * a.dt);
 #pragma unroll
         for (int k = 0; k < 5; ++k) D[k] = dn[k] + c * r[k];
@@ -317,8 +282,8 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p,
         double q[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            q[k] = a.rg_out.Qn[k * np + p] + w6 * (double)K[k];
-            a.rg_out.Qn[k * np + p] = q[k];
+            q[k] = a.Qn[k][p] + w6 * (double)K[k];
+            a.Qn[k][p] = q[k];
         }
         D[0] = (float)(q[0] - a.rho_b64[kg]);
         D[1] = (float)q[1];
@@ -326,7 +291,7 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, long long p,
         D[3] = (float)q[3];
         D[4] = (float)(q[4] - a.E_b64[kg]);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) a.rg_out.Dn[k * np + p] = D[k];
+        for (int k = 0; k < 5; ++k) a.Dn[k][p] = D[k];
     }
     prim_from_dev(a, p, kg, D);
 }
@@ -349,13 +314,13 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     const int x = rg.x0 + tx, y = rg.y0 + ty;
     const bool in_dom = x < nx && y < ny;
     const bool own = in_dom && x >= xs && y >= ys;
-    const long long np = a.np;
     // G_v planes are computed in increasing order; ghi is the last one, and
     // the ring holds the GSLOTS planes up to it
     int ghi = -1000;
 
     // ring bases of planes o-3 .. o+3, refreshed once per plane (plane o + d
-    // sits in slot (o + d) mod RING)
+    // sits in slot (o + d) mod RING; o+-3 share the slots of o-+2, and a
+    // stencil reaches o+-3 only next to a wall, where o-+2 lies outside the box)
     const T *pb0, *pb1, *pb2, *pb3, *pb4, *pb5, *pb6;
     auto pbase = [&](int k) -> const T * {  // k = d + 3, 0..6
         switch (k) {
@@ -389,7 +354,12 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
 
     PlaneLoad<T> pl;
     pl.init(a, rg);
-    for (int z = max(0, z0 - 3); z <= min(nz - 1, z0 + 3); ++z) {
+    // planes the first output plane needs: z0-2 .. z0+2, and up to z0+3
+    // (down to z0-3) when it is the bottom (top) wall, for the G_v plane two
+    // nodes in; later planes load one plane ahead, up to o+3, into the slot of
+    // o-2, which no later plane reads
+    int lhi = min(nz - 1, max(z0 + 2, 3));
+    for (int z = max(0, min(z0 - 2, nz - 4)); z <= lhi; ++z) {
         pl.issue(a, z);
         pl.finish(a, rg);
     }
@@ -447,7 +417,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         const int zw = wall_mode(o, nz);
         const int jlo = zw == 1 ? o : (zw == 2 ? o - 2 : o - 1);
         for (int j = max(ghi + 1, jlo); j <= jlo + 2; ++j) {
-            const int slot = j & (GSLOTS - 1);
+            const int slot = j % GSLOTS;
             ghi = j;
             if (in_dom) {
                 T G[4];
@@ -458,30 +428,31 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         }
         __syncthreads();
         // ---- 2. divergence, source, RK stage; next plane's primitives ----------
-        // plane o + 4 replaces o - 3, which no later plane needs
-        const bool next = o + 4 < nz && o + 1 < z1;
-        if (next) pl.issue(a, o + 4);
+        const int zn = lhi + 1;
+        const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
+        if (next) pl.issue(a, zn);
         if (own) {
-            const long long p = x + (long long)nx * (y + (long long)ny * o);
+            const int p = x + nx * (y + ny * o);
             T r[5];
             float kd[5], dn[5];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) r[k] = a.R[k * np + p];
-            const T w0 = a.W[p];
+            for (int k = 0; k < 5; ++k) r[k] = a.R[k][p];
+            const T w0 = a.W[0][p];
             if constexpr (sizeof(T) == 4) {
                 if (a.stage >= 2) {
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) kd[k] = a.rg_out.Kacc[k * np + p];
+                    for (int k = 0; k < 5; ++k) kd[k] = a.Kacc[k][p];
                 }
                 if (a.stage >= 1 && a.stage <= 3) {
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) dn[k] = a.rg_out.Dn[k * np + p];
+                    for (int k = 0; k < 5; ++k) dn[k] = a.Dn[k][p];
                 }
             }
             const int xm = wall_mode(x, nx), ym = wall_mode(y, ny);
             const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
-            const int sa = (o - 1) & (GSLOTS - 1), sb = (o + 1) & (GSLOTS - 1), s0 = o & (GSLOTS - 1);
-            const int sbb = (o + 2) & (GSLOTS - 1), saa = (o - 2) & (GSLOTS - 1);
+            // slots of G_v planes o-1, o+1, o, o+2, o-2 (GSLOTS = 3)
+            const int sa = (o + 2) % GSLOTS, sb = (o + 1) % GSLOTS, s0 = o % GSLOTS;
+            const int sbb = (o + 2) % GSLOTS, saa = (o + 1) % GSLOTS;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const T *e = EV + (k * TY + ty) * EW + tx + 1;
@@ -523,7 +494,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
             if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || o == 0 || o == nz - 1) r[1] = r[2] = r[3] = 0;
             if (a.stage == 0) {
 #pragma unroll
-                for (int k = 0; k < 5; ++k) a.rg_out.Rout[k * np + p] = r[k];
+                for (int k = 0; k < 5; ++k) a.Rout[k][p] = r[k];
             } else if constexpr (sizeof(T) == 4) {
                 mixed_update(a, p, kg, r, kd, dn);
             } else {
@@ -533,27 +504,31 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const double rk = (double)r[k];
-                    const long long i = k * np + p;
                     if (a.stage == 1) {
-                        const double q = a.rg_out.Qn[i];
-                        a.rg_out.acc[i] = q + bw * rk;
-                        a.rg_out.Qout[i] = q + cw * rk;
+                        const double q = a.Qn[k][p];
+                        a.acc[k][p] = q + bw * rk;
+                        a.Qout[k][p] = q + cw * rk;
                     } else if (a.stage < 4) {
-                        a.rg_out.acc[i] = a.rg_out.acc[i] + bw * rk;
-                        a.rg_out.Qout[i] = a.rg_out.Qn[i] + cw * rk;
+                        a.acc[k][p] = a.acc[k][p] + bw * rk;
+                        a.Qout[k][p] = a.Qn[k][p] + cw * rk;
                     } else {
-                        a.rg_out.Qout[i] = a.rg_out.acc[i] + bw * rk;
+                        a.Qout[k][p] = a.acc[k][p] + bw * rk;
                     }
                 }
             }
         }
-        if (next) pl.finish(a, rg);
+        if (next) {
+            pl.finish(a, rg);
+            lhi = zn;
+        }
         __syncthreads();
     }
 }
 
+// FP32: at most 64 registers, which with 56 KB of shared memory per block
+// keeps four blocks (32 warps) on an SM
 template <typename T>
-__global__ void __launch_bounds__(TX *TY) visc_rk_kernel(const VArgs<T> a)
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 4 : 2) visc_rk_kernel(const VArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     // blocks whose x and y ranges (with the one-node flux halo) stay off the
@@ -594,7 +569,7 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
         a.n[d] = bx.n[d];
         a.ih2[d] = (T)(0.5 * bx.inv_h[d]);
     }
-    a.np = bx.np;
+    a.np = (int)bx.np;
     a.ga = bx.ga;
     a.gm2 = (T)bx.gm2;
     a.iRe = (T)(1.0 / bx.Re);
@@ -604,7 +579,7 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
     a.c0 = (T)bx.mub_coef0;
     a.c1 = (T)bx.mub_coef1;
     a.g = (T)bx.g;
-    a.W = W;
+    for (int k = 0; k < 6; ++k) a.W[k] = W + (size_t)k * bx.np;
     if constexpr (sizeof(T) == 8) {
         a.rho_b = (const T *)bx.rho_b64;
         a.p_b = (const T *)bx.p_b64;
@@ -614,10 +589,19 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
     a.T_b = bx.T_b32;
     a.ip_b = bx.ip_b32;
     a.ir_b = bx.ir_b32;
-    a.R = R;
+    for (int k = 0; k < 5; ++k) a.R[k] = R + (size_t)k * bx.np;
     a.stage = stage;
     a.dt = bx.dt;
-    a.rg_out = g;
+    auto fp = [&](auto *base, int k) { return base ? base + (size_t)k * bx.np : base; };
+    for (int k = 0; k < 5; ++k) {
+        a.Rout[k] = fp(g.Rout, k);
+        a.Qn[k] = fp(g.Qn, k);
+        a.acc[k] = fp(g.acc, k);
+        a.Qout[k] = fp(g.Qout, k);
+        a.Kacc[k] = fp(g.Kacc, k);
+        a.Dn[k] = fp(g.Dn, k);
+    }
+    for (int k = 0; k < 6; ++k) a.Wn[k] = fp(g.Wn, k);
     a.rho_b64 = bx.rho_b64;
     a.E_b64 = bx.E_b64;
     a.gm1 = (float)(bx.gamma - 1.0);

@@ -396,6 +396,7 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     x.T_b32 = p32 + 3 * Ng;
     x.ip_b32 = p32 + 4 * Ng;
     x.ir_b32 = p32 + 5 * Ng;
+    x.err = ctx->dev_err;
 
     // state registers and scratch
     const size_t np = (size_t)x.np;
@@ -626,6 +627,7 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
+    if (e == cudaSuccess) e = init_tma_kernels();
     if (e == cudaSuccess) e = init_visc_kernels();
     if (e == cudaSuccess && (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO))
         e = init_gemm_kernels();

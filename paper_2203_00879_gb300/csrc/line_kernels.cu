@@ -18,7 +18,7 @@
 //   3. back-substitutes in place.
 // The block finally writes its own rows back (transposed again for x).
 // Sub-domains are independent, so no block waits for another.
-#include "nopcs_internal.cuh"
+#include "line_solve.cuh"
 
 namespace nopcs {
 
@@ -39,54 +39,12 @@ struct LineArgs {
     const T *b1;    // FLUX: H_b,   FILTER: E_b
 };
 
-template <typename T>
-__device__ __forceinline__ const T *coef_ptr(const LineOpDev &op);
-template <>
-__device__ __forceinline__ const double *coef_ptr<double>(const LineOpDev &op) { return op.coef64; }
-template <>
-__device__ __forceinline__ const float *coef_ptr<float>(const LineOpDev &op) { return op.coef32; }
-template <typename T>
-__device__ __forceinline__ const T *cp_ptr(const LineOpDev &op);
-template <>
-__device__ __forceinline__ const double *cp_ptr<double>(const LineOpDev &op) { return op.cp64; }
-template <>
-__device__ __forceinline__ const float *cp_ptr<float>(const LineOpDev &op) { return op.cp32; }
-template <typename T>
-__device__ __forceinline__ const T *inv_ptr(const LineOpDev &op);
-template <>
-__device__ __forceinline__ const double *inv_ptr<double>(const LineOpDev &op) { return op.inv64; }
-template <>
-__device__ __forceinline__ const float *inv_ptr<float>(const LineOpDev &op) { return op.inv32; }
-
-template <typename T>
-__device__ __forceinline__ T cp_limit(const LineOpDev &op) { return (T)op.cpL; }
-template <typename T>
-__device__ __forceinline__ T inv_limit(const LineOpDev &op) { return (T)op.invL; }
-
-// dot product of `len` taps with a column (stride LP), four partial sums
-template <typename T>
-__device__ __forceinline__ T dot_col(const T *c, const T *f, int len, int LP)
-{
-    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int k = 0;
-    for (; k + 4 <= len; k += 4) {
-        s0 += c[k] * f[(size_t)k * LP];
-        s1 += c[k + 1] * f[(size_t)(k + 1) * LP];
-        s2 += c[k + 2] * f[(size_t)(k + 2) * LP];
-        s3 += c[k + 3] * f[(size_t)(k + 3) * LP];
-    }
-    for (; k < len; ++k) s0 += c[k] * f[(size_t)k * LP];
-    return (s0 + s1) + (s2 + s3);
-}
-
 template <typename T, int MODE, int AXIS>
 __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
     constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
-    constexpr int W = MODE == MODE_FILTER ? 3 : 2;     // right-hand-side half-width
-    constexpr int NEXP = MODE == MODE_FILTER ? 3 : 2;  // explicit rows at each wall
     constexpr int U = 4;                               // loads in flight per thread and pass
     const int LINES = a.lines, LP = a.lines + 1, RT = a.rt;
     const int KC = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
@@ -108,8 +66,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 
     const int *rec = op.sub + b * SUB_REC;
     const int s = rec[0], e = rec[1], tlo = rec[2], thi = rec[3];
-    const int j0s = rec[4], lens = rec[5], j0e = rec[7], lene = rec[8];
-    const int lo = rec[10], hi = rec[11];
+    const int lens = rec[5], lene = rec[8];
     const int nrows = thi - tlo + 1;
     const int srow = AXIS == 0 ? 1 : (AXIS == 1 ? nx : nx * ny);
     const int sa = AXIS == 0 ? nx : 1;
@@ -198,103 +155,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     // ---- per-(line, field) NOHAP solve ----------------------------------------
     const int l = threadIdx.x % LINES;
     const int fld = threadIdx.x / LINES;
-    if (l < nl && fld < NF) {
-        T *col = sm + (size_t)fld * fs + l;  // row r at col[(r - tlo) * LP]
-        const int N = op.N;
-        // 1. end rows from the equivalent explicit scheme (Eq. CS:fpCf_i)
-        const T gs = dot_col(cs, col + (size_t)(j0s - tlo) * LP, lens, LP);
-        const T ge = lene > 0 ? dot_col(ce, col + (size_t)(j0e - tlo) * LP, lene, LP) : T(0);
-        // explicit wall-closure rows strictly inside the sub-domain
-        T exL[NEXP], exH[NEXP];
-#pragma unroll
-        for (int r = 0; r < NEXP; ++r) {
-            exL[r] = 0;
-            exH[r] = 0;
-            if (r > s && r < e) {
-                T acc = 0;
-#pragma unroll
-                for (int j = 0; j < 5; ++j)
-                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * col[(size_t)(j - tlo) * LP];
-                exL[r] = acc;
-            }
-            const int rh = N - 1 - r;
-            if (rh > s && rh < e) {
-                T acc = 0;
-#pragma unroll
-                for (int j = 0; j < 5; ++j)
-                    if (op.ex[r][j] != 0.0) acc += (T)op.ex[r][j] * col[(size_t)(N - 1 - j - tlo) * LP];
-                exH[r] = (T)op.ex_sign * acc;
-            }
-        }
-        // 2./3. Thomas over the implicit rows lo..hi; forward values overwrite
-        // the staged inputs, which a register window of 2W+1 keeps
-        if (lo <= hi) {
-            const int m = hi - lo + 1;
-            const T al = (T)op.alpha;
-            const T gL = lo == s + 1 ? gs : exL[NEXP - 1];
-            const T gR = hi == e - 1 ? ge : exH[NEXP - 1];
-            const T r0 = (T)op.rb[0], r1 = (T)op.rb[1], r2 = (T)op.rb[2], r3 = (T)op.rb[3];
-            const T cL = cp_limit<T>(op), iL = inv_limit<T>(op);
-            T win[2 * W + 1];
-            const T *pin = col + (size_t)(lo - W - tlo) * LP;
-#pragma unroll
-            for (int j = 0; j < 2 * W; ++j) win[j] = pin[(size_t)j * LP];
-            pin += (size_t)(2 * W) * LP;                // row lo + W
-            T *pout = col + (size_t)(lo - tlo) * LP;   // row lo
-            T dprev = 0;
-            // one forward row: right-hand side from the window, minus the
-            // coupling `adj` to a known end value, then the elimination
-            auto fwd = [&](T iv, T adj) {
-                win[2 * W] = *pin;
-                pin += LP;
-                T rhs;
-                if constexpr (MODE == MODE_FILTER)
-                    rhs = r0 * win[3] + r1 * (win[4] + win[2]) + r2 * (win[5] + win[1]) + r3 * (win[6] + win[0]);
-                else
-                    rhs = r0 * (win[3] - win[1]) + r1 * (win[4] - win[0]);
-                const T dp = (rhs - adj - al * dprev) * iv;
-                *pout = dp;
-                pout += LP;
-                dprev = dp;
-#pragma unroll
-                for (int j = 0; j < 2 * W; ++j) win[j] = win[j + 1];
-            };
-            // first row carries the left end value (and the right one if m == 1)
-            fwd(tiv[0], al * gL + (m == 1 ? al * gR : T(0)));
-            const int kmid = min(KC, m - 1);
-            int r = 1;
-#pragma unroll 4
-            for (; r < kmid; ++r) fwd(tiv[r], T(0));
-#pragma unroll 4
-            for (; r < m - 1; ++r) fwd(iL, T(0));
-            if (m > 1) fwd(m - 1 < KC ? tiv[m - 1] : iL, al * gR);
-            // back substitution from row hi - 1 down to lo
-            T x = dprev;
-            pout -= 2 * (size_t)LP;  // row hi - 1
-            r = m - 2;
-#pragma unroll 4
-            for (; r >= KC; --r) {
-                x = *pout - cL * x;
-                *pout = x;
-                pout -= LP;
-            }
-#pragma unroll 4
-            for (; r >= 0; --r) {
-                x = *pout - tcp[r] * x;
-                *pout = x;
-                pout -= LP;
-            }
-        }
-        // explicit values into their rows
-        col[(size_t)(s - tlo) * LP] = gs;
-        if (lene > 0) col[(size_t)(e - tlo) * LP] = ge;
-#pragma unroll
-        for (int r = 0; r < NEXP; ++r) {
-            if (r > s && r < e) col[(size_t)(r - tlo) * LP] = exL[r];
-            const int rh = N - 1 - r;
-            if (rh > s && rh < e) col[(size_t)(rh - tlo) * LP] = exH[r];
-        }
-    }
+    if (l < nl && fld < NF) nohap_solve_column<T, MODE, false>(op, sm + (size_t)fld * fs + l, LP, cs, ce, tcp, tiv, KC, rec, T(1));
     __syncthreads();
 
     // ---- write the sub-domain's own rows ---------------------------------------
@@ -383,13 +244,13 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     long long nblk = (long long)op.nsub * a.ntile_a * Nc;
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    // at least 256 threads: the extra ones only stage and store, which keeps
-    // more loads in flight per SM
     // extra threads beyond the lines x fields of the solve only stage and
-    // store, which keeps more loads in flight per SM
+    // store, which keeps more loads in flight per SM (8 per line for the five
+    // flux fields, 4 per line for one field: the fastest on GB300)
     int threads = a.lines * NF;
     threads = (threads + 31) / 32 * 32;
-    if (threads < 8 * a.lines) threads = 8 * a.lines;
+    const int per_line = NF == 1 ? 4 : 8;
+    if (threads < per_line * a.lines) threads = per_line * a.lines;
     if (threads < 128) threads = 128;
     if (threads > 1024) threads = (a.lines * NF + 31) / 32 * 32;
     if (threads > 1024) return cudaErrorInvalidConfiguration;
@@ -448,6 +309,9 @@ template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
                              int first, cudaStream_t st, int lines)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (flux_tma_usable(op, bx, axis, W, R)) return launch_flux_tma(op, axis, bx, W, R, first, st);
+    }
     LineArgs<T> a{};
     for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
     for (int k = 0; k < 6; ++k) a.in[k] = W + (size_t)k * bx.np;

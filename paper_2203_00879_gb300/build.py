@@ -65,8 +65,8 @@ if __name__ == "__main__":
 
 KERNEL_FILES = {
     "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu"], "diagnostics": ["rk_kernels.cu"],
-    "sweep_x": ["line_kernels.cu", "line_solve.cuh"], "sweep_y": ["line_kernels.cu", "line_tma.cu", "line_solve.cuh"],
-    "sweep_z": ["line_kernels.cu", "line_tma.cu", "line_solve.cuh"],
+    "sweep_x": ["line_kernels.cu", "line_solve.cuh"], "sweep_y": ["line_kernels.cu", "line_solve.cuh"],
+    "sweep_z": ["line_kernels.cu", "line_solve.cuh"],
     "filter": ["line_kernels.cu", "line_solve.cuh"], "visc_rk_update": ["visc_kernel.cu"],
 }
 

@@ -627,7 +627,6 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
-    if (e == cudaSuccess) e = init_tma_kernels();
     if (e == cudaSuccess) e = init_visc_kernels();
     if (e == cudaSuccess && (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO))
         e = init_gemm_kernels();

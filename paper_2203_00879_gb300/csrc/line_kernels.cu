@@ -309,9 +309,6 @@ template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
                              int first, cudaStream_t st, int lines)
 {
-    if constexpr (sizeof(T) == 4) {
-        if (flux_tma_usable(op, bx, axis, W, R)) return launch_flux_tma(op, axis, bx, W, R, first, st);
-    }
     LineArgs<T> a{};
     for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
     for (int k = 0; k < 6; ++k) a.in[k] = W + (size_t)k * bx.np;

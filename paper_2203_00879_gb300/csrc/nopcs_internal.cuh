@@ -134,13 +134,6 @@ cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], con
 template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
                              int first, cudaStream_t st, int lines = 0);
-// FLUX along y or z in FP32 with TMA staging (line_tma.cu): usable when x is
-// a multiple of 4 points and the tile fits; otherwise launch_line_flux stays
-// on the register-staged kernel.
-bool flux_tma_usable(const LineOpDev &op, const BoxDev &bx, int axis, const void *W, const void *R);
-cudaError_t launch_flux_tma(const LineOpDev &op, int axis, const BoxDev &bx, const float *W, float *R, int first,
-                            cudaStream_t st);
-cudaError_t init_tma_kernels();
 // FILTER (FP64): Qout = L(Q - base) + base, 5 fields.
 cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
                                const double *Qin, double *Qout, cudaStream_t st);

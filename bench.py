@@ -341,6 +341,7 @@ def main():
     npts = float(n) ** 3
     p = box(n, args.sub_n, seed=1 + rank)
     ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=st)
+    tile_lines = N.nopcs_box_info(ctx, 0)["tile_lines"]
     N.nopcs_rk_step(ctx, W)
     N.nopcs_synchronize(ctx)
     N.nopcs_set_profiling(ctx, True)
@@ -458,6 +459,7 @@ def main():
                                    "NOHAP derivatives, FP64 state and RK4), sub-domains of %d, filter every 50 "
                                    "steps" % (n, args.sub_n),
                        "grid": [n, n, n], "sub_n": args.sub_n, "precision": "mixed", "form": "thomas",
+                       "sweep_tile_lines": tile_lines,
                        "l2": "inputs larger than L2 (FP64 state %.1f GB)" % (40 * npts / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -207,12 +207,13 @@ nopcs_status nopcs_filter(nopcs_ctx *ctx, int box);
 nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out);
 
 /*
- * Choices in force for box `box` (caller arrays of 3 ints, either may be
- * NULL): the sub-domain length per axis (the autotuner's pick where the
- * descriptor asked for -1) and the form of the FP32 derivative per axis
- * (NOPCS_FORM_THOMAS or NOPCS_FORM_GEMM_3XTF32).
+ * Choices in force for box `box` (caller arrays of 3 ints, any may be NULL):
+ * the sub-domain length per axis (the autotuner's pick where the descriptor
+ * asked for -1), the form of the FP32 derivative per axis (NOPCS_FORM_THOMAS
+ * or NOPCS_FORM_GEMM_3XTF32) and the flux sweeps' tile width per axis (grid
+ * lines per CUDA block; 0 = the precision's default, untuned for small boxes).
  */
-nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form);
+nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form, int *tile_lines);
 
 /* Wait for all work enqueued on the context stream. */
 nopcs_status nopcs_synchronize(nopcs_ctx *ctx);

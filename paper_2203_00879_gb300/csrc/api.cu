@@ -872,7 +872,7 @@ nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out)
     return NOPCS_OK;
 }
 
-nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form)
+nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form, int *tile_lines)
 {
     nopcs_status s = check_box(ctx, box);
     if (s != NOPCS_OK) return s;
@@ -880,6 +880,7 @@ nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form
     for (int a = 0; a < 3; ++a) {
         if (sub_n) sub_n[a] = b.sub_n[a];
         if (deriv_form) deriv_form[a] = b.deriv_gemm[a] ? NOPCS_FORM_GEMM_3XTF32 : NOPCS_FORM_THOMAS;
+        if (tile_lines) tile_lines[a] = b.lines[a];
     }
     return NOPCS_OK;
 }

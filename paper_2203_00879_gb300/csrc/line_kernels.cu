@@ -27,7 +27,8 @@ struct LineArgs {
     int n[3];
     int lines;      // lines per block (LINES)
     int ntile_a;    // tiles along the line-tile axis
-    int rt;         // row capacity of a field column (op.max_tile)
+    int rt;         // staged-row capacity (op.max_tile): tile rows along x
+    int rw;         // solve-window capacity (op.max_win): tile rows along y, z
     // one base pointer per field, so a node is one 32-bit index away from a
     // kernel parameter (fields hold < 2^31 points)
     const T *in[6]; // FIELD: f; FLUX: W (6 fields); FILTER: Q (5 fields)
@@ -46,14 +47,23 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
     constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
     constexpr int U = 4;                               // loads in flight per thread and pass
-    const int LINES = a.lines, LP = a.lines + 1, RT = a.rt;
+    // y, z: the end-row dot products are summed while staging (STREAM) and
+    // only the solve window is kept; x: the whole staged tile is kept and the
+    // solve takes the dot products from it (a warp walks one line at a time
+    // there, and a per-line warp reduction costs more than it saves)
+    constexpr bool STREAM = AXIS != 0;
+    const int LINES = a.lines, LP = a.lines + 1, RW = STREAM ? a.rw : a.rt;
     const int KC = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
-    // shared memory: end-row taps (2 x max_taps), Thomas factors (2 x KC), tile
+    // row groups sharing a line while staging along y, z
+    const int RG = STREAM ? (int)blockDim.x / LINES : 0;
+    // shared memory: end-row taps (2 x max_taps), Thomas factors (2 x KC),
+    // end-row partial sums [RG][2][NF][LINES], tile [NF][RW][LP]
     T *cs = reinterpret_cast<T *>(smraw);
     T *ce = cs + op.max_taps;
     T *tcp = ce + op.max_taps;
     T *tiv = tcp + KC;
-    T *sm = tiv + KC;
+    T *part = tiv + KC;
+    T *sm = part + (size_t)RG * 2 * NF * LINES;
     const int nx = a.n[0], ny = a.n[1];
 
     const int b = blockIdx.x % op.nsub;
@@ -66,7 +76,8 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 
     const int *rec = op.sub + b * SUB_REC;
     const int s = rec[0], e = rec[1], tlo = rec[2], thi = rec[3];
-    const int lens = rec[5], lene = rec[8];
+    const int j0s = rec[4], lens = rec[5], j0e = rec[7], lene = rec[8];
+    const int org = STREAM ? rec[12] : tlo, last = STREAM ? rec[13] : thi;  // tile rows
     const int nrows = thi - tlo + 1;
     const int srow = AXIS == 0 ? 1 : (AXIS == 1 ? nx : nx * ny);
     const int sa = AXIS == 0 ? nx : 1;
@@ -74,13 +85,17 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     const int gbase = cc * sc + a0 * sa + tlo * srow;
     // which of (row, line, cc) is the coordinate along the gravity axis
     const int gsel = a.ga == AXIS ? 0 : (a.ga == (AXIS == 0 ? 1 : 0) ? 1 : 2);
-    const size_t fs = (size_t)RT * LP;
+    const size_t fs = (size_t)RW * LP;
 
     // ---- block constants: end-row taps and the unconverged Thomas factors ----
+    // (STREAM reads the taps from the global table while staging: no barrier
+    // between these loads and the staging loads)
+    const T *coef = coef_ptr<T>(op);
     {
-        const T *coef = coef_ptr<T>(op);
-        for (int k = threadIdx.x; k < lens; k += blockDim.x) cs[k] = coef[rec[6] + k];
-        for (int k = threadIdx.x; k < lene; k += blockDim.x) ce[k] = coef[rec[9] + k];
+        if (!STREAM) {
+            for (int k = threadIdx.x; k < lens; k += blockDim.x) cs[k] = coef[rec[6] + k];
+            for (int k = threadIdx.x; k < lene; k += blockDim.x) ce[k] = coef[rec[9] + k];
+        }
         const T *cpp = cp_ptr<T>(op), *ivp = inv_ptr<T>(op);
         for (int k = threadIdx.x; k < KC; k += blockDim.x) {
             tcp[k] = cpp[k];
@@ -88,7 +103,11 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
         }
     }
 
-    // ---- stage rows [tlo, thi] of nl lines into [field][row][line] -----------
+    // ---- stage rows [tlo, thi] of nl lines --------------------------------------
+    // Rows [org, last] go to the tile [field][row][line].  STREAM: every
+    // staged row also feeds the two end-row dot products
+    // g_i = sum_j C_ij f_j (Eq. CS:fpCf_i) as it passes, so the end-row
+    // supports outside the solve window need no shared memory.
     // x: a warp walks the rows of one line (coalesced along x, transposed into
     // the odd line pitch); y, z: consecutive threads take consecutive lines.
     {
@@ -102,13 +121,16 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             l0 = threadIdx.x % LINES;
             lstep = LINES;  // one line per thread
             r0 = threadIdx.x / LINES;
-            rstep = blockDim.x / LINES;
+            rstep = RG;
+            if (r0 >= RG) l0 = LINES;  // threads beyond RG x LINES do not stage
         }
-        for (int l = l0; l < nl; l += lstep) {
+        for (int l = l0; l < (AXIS == 0 ? nl : LINES); l += lstep) {
             const int src = gbase + l * sa;
-            T *dst = sm + l;
             const int gl = gsel == 1 ? a0 + l : cc;
-            for (int r = r0; r < nrows; r += U * rstep) {
+            T ps[NF], pe[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) ps[f] = pe[f] = T(0);
+            for (int r = r0; l < nl && r < nrows; r += U * rstep) {
                 T v[U][NIN];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -123,29 +145,56 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                 for (int u = 0; u < U; ++u) {
                     const int rr = r + u * rstep;
                     if (rr >= nrows) continue;
-                    T *d = dst + (size_t)rr * LP;
+                    const int g = tlo + rr;
+                    T val[NF];
                     if constexpr (MODE == MODE_FIELD) {
-                        d[0] = v[u][0];
+                        val[0] = v[u][0];
                     } else if constexpr (MODE == MODE_FLUX) {
-                        const int gk = gsel == 0 ? tlo + rr : gl;
+                        const int gk = gsel == 0 ? g : gl;
                         const T rho = a.b0[gk] + v[u][0];
                         const T uu = v[u][1], vv = v[u][2], ww = v[u][3], pp = v[u][4];
                         const T H = a.b1[gk] + v[u][5];
                         const T ud = AXIS == 0 ? uu : (AXIS == 1 ? vv : ww);
                         const T m = rho * ud;
-                        d[0] = m;
-                        d[fs] = m * uu + (AXIS == 0 ? pp : T(0));
-                        d[2 * fs] = m * vv + (AXIS == 1 ? pp : T(0));
-                        d[3 * fs] = m * ww + (AXIS == 2 ? pp : T(0));
-                        d[4 * fs] = H * ud;
+                        val[0] = m;
+                        val[1] = m * uu + (AXIS == 0 ? pp : T(0));
+                        val[2] = m * vv + (AXIS == 1 ? pp : T(0));
+                        val[3] = m * ww + (AXIS == 2 ? pp : T(0));
+                        val[4] = H * ud;
                     } else {  // FILTER on Q - base
-                        const int gk = gsel == 0 ? tlo + rr : gl;
-                        d[0] = v[u][0] - a.b0[gk];
-                        d[fs] = v[u][1];
-                        d[2 * fs] = v[u][2];
-                        d[3 * fs] = v[u][3];
-                        d[4 * fs] = v[u][4] - a.b1[gk];
+                        const int gk = gsel == 0 ? g : gl;
+                        val[0] = v[u][0] - a.b0[gk];
+                        val[1] = v[u][1];
+                        val[2] = v[u][2];
+                        val[3] = v[u][3];
+                        val[4] = v[u][4] - a.b1[gk];
                     }
+                    if (!STREAM || (g >= org && g <= last)) {
+                        T *d = sm + (size_t)(g - org) * LP + l;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) d[f * fs] = val[f];
+                    }
+                    if constexpr (STREAM) {
+                        const unsigned ks = (unsigned)(g - j0s), ke = (unsigned)(g - j0e);
+                        if (ks < (unsigned)lens) {
+                            const T c = __ldg(coef + rec[6] + ks);
+#pragma unroll
+                            for (int f = 0; f < NF; ++f) ps[f] += c * val[f];
+                        }
+                        if (ke < (unsigned)lene) {
+                            const T c = __ldg(coef + rec[9] + ke);
+#pragma unroll
+                            for (int f = 0; f < NF; ++f) pe[f] += c * val[f];
+                        }
+                    }
+                }
+            }
+            if constexpr (STREAM) {
+                T *pp = part + l + (size_t)r0 * 2 * NF * LINES;  // [k][which][f][line]
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    pp[(size_t)f * LINES] = ps[f];
+                    pp[(size_t)(NF + f) * LINES] = pe[f];
                 }
             }
         }
@@ -153,9 +202,24 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     __syncthreads();
 
     // ---- per-(line, field) NOHAP solve ----------------------------------------
-    const int l = threadIdx.x % LINES;
-    const int fld = threadIdx.x / LINES;
-    if (l < nl && fld < NF) nohap_solve_column<T, MODE, false>(op, sm + (size_t)fld * fs + l, LP, cs, ce, tcp, tiv, KC, rec, T(1));
+    {
+        const int l = threadIdx.x % LINES;
+        const int fld = threadIdx.x / LINES;
+        if (l < nl && fld < NF) {
+            T *col = sm + (size_t)fld * fs + l;
+            T gs = 0, ge = 0;
+            if constexpr (STREAM) {
+                for (int k = 0; k < RG; ++k) {
+                    gs += part[((size_t)k * 2 * NF + fld) * LINES + l];
+                    ge += part[((size_t)k * 2 * NF + NF + fld) * LINES + l];
+                }
+            } else {
+                gs = dot_col(cs, col + (size_t)(j0s - org) * LP, lens, LP);
+                if (lene > 0) ge = dot_col(ce, col + (size_t)(j0e - org) * LP, lene, LP);
+            }
+            nohap_solve_column<T, MODE, false>(op, col, LP, org, gs, ge, tcp, tiv, KC, rec, T(1));
+        }
+    }
     __syncthreads();
 
     // ---- write the sub-domain's own rows ---------------------------------------
@@ -176,7 +240,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
         const int obase = gbase + (s - tlo) * srow;
         for (int ll = l0; ll < nl; ll += lstep) {
             const int dstg = obase + ll * sa;
-            const T *srcs = sm + (size_t)(s - tlo) * LP + ll;
+            const T *srcs = sm + (size_t)(s - org) * LP + ll;
             const int gl = gsel == 1 ? a0 + ll : cc;
             for (int r = r0; r < nown; r += U * rstep) {
                 T old[U][5];
@@ -222,10 +286,10 @@ namespace {
 
 constexpr size_t SMEM_BUDGET = 200 * 1024;
 
-int pick_lines(int pref, int rt, int nf, size_t esz)
+int pick_lines(int pref, int rw, int nf, size_t esz)
 {
     int L = pref;
-    while (L > 1 && (size_t)nf * rt * (L + 1) * esz > SMEM_BUDGET) L /= 2;
+    while (L > 1 && (size_t)nf * rw * (L + 1) * esz > SMEM_BUDGET) L /= 2;
     return L;
 }
 
@@ -234,10 +298,10 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
 {
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
     a.rt = op.max_tile;
-    a.lines = pick_lines(pref_lines, a.rt, NF, sizeof(T));
+    a.rw = op.max_win;
+    const int rows = AXIS == 0 ? a.rt : a.rw;
+    a.lines = pick_lines(pref_lines, rows, NF, sizeof(T));
     const int kc = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
-    size_t smem = ((size_t)NF * a.rt * (a.lines + 1) + 2 * (size_t)op.max_taps + 2 * (size_t)kc) * sizeof(T);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int Na = AXIS == 0 ? a.n[1] : a.n[0];
     const int Nc = AXIS == 2 ? a.n[1] : a.n[2];
     a.ntile_a = (Na + a.lines - 1) / a.lines;
@@ -254,6 +318,11 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     if (threads < 128) threads = 128;
     if (threads > 1024) threads = (a.lines * NF + 31) / 32 * 32;
     if (threads > 1024) return cudaErrorInvalidConfiguration;
+    const int rg = AXIS == 0 ? 0 : threads / a.lines;
+    const size_t smem = ((size_t)NF * rows * (a.lines + 1) + 2 * (size_t)op.max_taps + 2 * (size_t)kc +
+                         (size_t)rg * 2 * NF * a.lines) *
+                        sizeof(T);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     line_kernel<T, MODE, AXIS><<<(unsigned)nblk, threads, smem, st>>>(op, a);
     return cudaGetLastError();
 }

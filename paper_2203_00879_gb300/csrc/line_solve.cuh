@@ -1,11 +1,10 @@
-// NOHAP solve of one staged column (arXiv 2203.00879, Sec. 3), shared by the
-// register-staged and the TMA-staged line kernels.
+// NOHAP solve of one staged column (arXiv 2203.00879, Sec. 3).
 //
-// A column holds rows tlo .. thi of one (line, field) pair in shared memory,
-// row r at col[(r - tlo) * LP].  The solve
-//   1. evaluates the sub-domain's two end values with the equivalent explicit
-//      rows g_i = sum_j C_ij f_j (Eq. CS:fpCf_i) and any explicit wall-closure
-//      row inside the sub-domain,
+// A column holds (at least) the solve window win_lo .. win_hi of one (line,
+// field) pair in shared memory, row r at col[(r - org) * LP].  Given the sub-domain's
+// two end values (the equivalent explicit rows g_i = sum_j C_ij f_j of
+// Eq. CS:fpCf_i, evaluated by the caller) the solve
+//   1. evaluates any explicit wall-closure row inside the sub-domain,
 //   2. runs the Thomas forward sweep over the implicit rows (tabulated factors,
 //      the end values moved to the right-hand side), keeping the last 2W+1
 //      inputs in registers and writing the forward values in place,
@@ -53,22 +52,20 @@ __device__ __forceinline__ T dot_col(const T *c, const T *f, int len, int LP)
     return (s0 + s1) + (s2 + s3);
 }
 
-// cs / ce: the end-row taps of the sub-domain (record rec); tcp / tiv: the
-// first KC Thomas factors (the rest equal their limits cpL / invL).
+// org: the row at col[0]; gs / ge: the end values at rows s and e (ge unused
+// when e == s); tcp / tiv: the first KC Thomas factors (the rest equal their
+// limits cpL / invL).
 template <typename T, int MODE, bool SCALED>
-__device__ __forceinline__ void nohap_solve_column(const LineOpDev &op, T *col, int LP, const T *cs, const T *ce,
+__device__ __forceinline__ void nohap_solve_column(const LineOpDev &op, T *col, int LP, int org, T gs, T ge,
                                                    const T *tcp, const T *tiv, int KC, const int *rec, T osc)
 {
     constexpr int W = MODE == MODE_FILTER ? 3 : 2;     // right-hand-side half-width
     constexpr int NEXP = MODE == MODE_FILTER ? 3 : 2;  // explicit rows at each wall
-    const int s = rec[0], e = rec[1], tlo = rec[2];
-    const int j0s = rec[4], lens = rec[5], j0e = rec[7], lene = rec[8];
+    const int s = rec[0], e = rec[1], tlo = org;
+    const int lene = rec[8];
     const int lo = rec[10], hi = rec[11];
     const int N = op.N;
     auto out = [&](T v) { return SCALED ? v * osc : v; };
-    // 1. end rows from the equivalent explicit scheme (Eq. CS:fpCf_i)
-    const T gs = dot_col(cs, col + (size_t)(j0s - tlo) * LP, lens, LP);
-    const T ge = lene > 0 ? dot_col(ce, col + (size_t)(j0e - tlo) * LP, lene, LP) : T(0);
     // explicit wall-closure rows strictly inside the sub-domain
     T exL[NEXP], exH[NEXP];
 #pragma unroll

@@ -21,12 +21,14 @@ enum LineMode { MODE_FIELD = 0, MODE_FLUX = 1, MODE_FILTER = 2 };
 //   [4] j0_s, [5] len_s, [6] off_s   end row at s: first column, taps, offset in coef
 //   [7] j0_e, [8] len_e, [9] off_e   end row at e
 //   [10] lo, [11] hi         implicit rows solved by Thomas (lo > hi: none)
-constexpr int SUB_REC = 12;
+//   [12] win_lo, [13] win_hi rows the solve reads (the end-row supports
+//                            outside them are consumed while staging)
+constexpr int SUB_REC = 14;
 
 // Host copy of a line operator (Sec. 3): partition, end rows, Thomas factors.
 struct LineOpHost {
     int N = 0, nsub = 0, nexp = 0, kind = 0, sub_n = 0;
-    int maxm = 0, max_tile = 0;
+    int maxm = 0, max_tile = 0, max_win = 0;
     double thresh = 0.0, alpha = 0.0;
     double rb[4] = {0, 0, 0, 0};  // interior right-hand-side weights
     double ex[3][5] = {};         // explicit rows next to the low wall (taps at 0..4)
@@ -40,7 +42,7 @@ struct LineOpHost {
 
 // Device view passed by value to the line kernels.
 struct LineOpDev {
-    int N, nsub, nexp, maxm, max_tile, max_taps;
+    int N, nsub, nexp, maxm, max_tile, max_taps, max_win;
     int kconv64, kconv32;
     double cpL, invL;  // limits of the Thomas factors
     double alpha;

@@ -237,26 +237,37 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
         int hi = e - 1 < N - 1 - op.nexp ? e - 1 : N - 1 - op.nexp;
         rec[10] = lo;
         rec[11] = hi;
-        // rows the block must stage
-        int tlo = s, thi = e;
+        // rows the solve reads (window) and rows the block must stage (the
+        // window plus the end-row supports)
+        int wlo = s, whi = e;
+        auto cover_w = [&](int a, int c) {
+            if (a < wlo) wlo = a;
+            if (c > whi) whi = c;
+        };
+        if (lo <= hi) cover_w(lo - w, hi + w);
+        for (int r = 0; r < op.nexp; ++r) {
+            if (r > s && r < e) cover_w(0, 4 < N - 1 ? 4 : N - 1);
+            if (N - 1 - r > s && N - 1 - r < e) cover_w(N - 5 > 0 ? N - 5 : 0, N - 1);
+        }
+        if (wlo < 0) wlo = 0;
+        if (whi > N - 1) whi = N - 1;
+        int tlo = wlo, thi = whi;
         auto cover = [&](int a, int c) {
             if (a < tlo) tlo = a;
             if (c > thi) thi = c;
         };
         cover(rec[4], rec[4] + rec[5] - 1);
         if (rec[8] > 0) cover(rec[7], rec[7] + rec[8] - 1);
-        if (lo <= hi) cover(lo - w, hi + w);
-        for (int r = 0; r < op.nexp; ++r) {
-            if (r > s && r < e) cover(0, 4 < N - 1 ? 4 : N - 1);
-            if (N - 1 - r > s && N - 1 - r < e) cover(N - 5 > 0 ? N - 5 : 0, N - 1);
-        }
         if (tlo < 0) tlo = 0;
         if (thi > N - 1) thi = N - 1;
         rec[2] = tlo;
         rec[3] = thi;
+        rec[12] = wlo;
+        rec[13] = whi;
         int m = hi - lo + 1;
         if (m > op.maxm) op.maxm = m;
         if (thi - tlo + 1 > op.max_tile) op.max_tile = thi - tlo + 1;
+        if (whi - wlo + 1 > op.max_win) op.max_win = whi - wlo + 1;
     }
     // Thomas factors for a run of implicit rows after a known value
     int mm = op.maxm > 0 ? op.maxm : 1;
@@ -423,6 +434,7 @@ cudaError_t LineOpBuf::upload()
     dev.nexp = h.nexp;
     dev.maxm = h.maxm;
     dev.max_tile = h.max_tile;
+    dev.max_win = h.max_win;
     dev.max_taps = h.max_taps;
     dev.kconv64 = h.kconv64;
     dev.kconv32 = h.kconv32;

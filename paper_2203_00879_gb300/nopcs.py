@@ -62,7 +62,7 @@ _L.nopcs_rhs.argtypes = [_vp, _i, _vp, _vp]
 _L.nopcs_filter.argtypes = [_vp, _i]
 _L.nopcs_diagnostics.argtypes = [_vp, _i, C.POINTER(nopcs_diag)]
 _L.nopcs_synchronize.argtypes = [_vp]
-_L.nopcs_box_info.argtypes = [_vp, _i, _vp, _vp]
+_L.nopcs_box_info.argtypes = [_vp, _i, _vp, _vp, _vp]
 _L.nopcs_set_profiling.argtypes = [_vp, _i]
 _L.nopcs_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _i]
 _L.nopcs_kernel_name.argtypes = [_i]
@@ -163,11 +163,13 @@ def nopcs_diagnostics(ctx, box: int, allow_unstable: bool = False) -> dict:
 
 
 def nopcs_box_info(ctx, box: int) -> dict:
-    """Sub-domain length and FP32-derivative form in force per axis."""
+    """Sub-domain length, FP32-derivative form and flux-sweep tile width in
+    force per axis."""
     sub = (_i * 3)()
     form = (_i * 3)()
-    _check(ctx, _L.nopcs_box_info(ctx, box, sub, form))
-    return {"sub_n": list(sub), "deriv_form": list(form)}
+    lines = (_i * 3)()
+    _check(ctx, _L.nopcs_box_info(ctx, box, sub, form, lines))
+    return {"sub_n": list(sub), "deriv_form": list(form), "tile_lines": list(lines)}
 
 
 def nopcs_synchronize(ctx) -> None:

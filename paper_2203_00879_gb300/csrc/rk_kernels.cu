@@ -292,7 +292,7 @@ __global__ void initial_state_kernel(const BoxDev bx, unsigned long long seed, d
 
 // ---------------------------------------------------------------------------
 // Diagnostics: per-block partials (fixed grid, fixed order), then one block.
-// partial record: mass, mx, my, mz, energy, max|V|, max|dp|, max Mach, bad
+// partial record: mass, mx, my, mz, energy, max|V|^2, max|dp|, max Mach^2, bad
 // ---------------------------------------------------------------------------
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_REC = 10;
@@ -344,18 +344,33 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
 
 __global__ void diag_final_kernel(const BoxDev bx, const double *partial, int nblk, double *out)
 {
-    if (threadIdx.x != 0) return;
+    // one block: each thread folds a fixed stride of partial records, then a
+    // fixed-shape tree; the reduction order never changes between calls
+    __shared__ double sh[DIAG_REC][DIAG_THREADS];
     double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         const double *q = partial + (size_t)b * DIAG_REC;
         for (int k = 0; k < 5; ++k) v[k] += q[k];
         for (int k = 5; k < 9; ++k) v[k] = fmax(v[k], q[k]);
     }
-    const double dV = bx.h[0] * bx.h[1] * bx.h[2];
-    for (int k = 0; k < 5; ++k) v[k] *= dV;
-    v[5] = sqrt(v[5]);
-    v[7] = sqrt(v[7]);
-    for (int k = 0; k < DIAG_REC; ++k) out[k] = v[k];
+    for (int k = 0; k < DIAG_REC; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+            for (int k = 5; k < 9; ++k) sh[k][threadIdx.x] = fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double dV = bx.h[0] * bx.h[1] * bx.h[2];
+        for (int k = 0; k < 5; ++k) out[k] = sh[k][0] * dV;
+        out[5] = sqrt(sh[5][0]);
+        out[6] = sh[6][0];
+        out[7] = sqrt(sh[7][0]);
+        out[8] = sh[8][0];
+        out[9] = 0.0;
+    }
 }
 
 int grid_for(long long work, int threads)
@@ -406,7 +421,7 @@ cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partia
     diag_partial_kernel<<<nblk, DIAG_THREADS, 0, st>>>(bx, Q, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    diag_final_kernel<<<1, 32, 0, st>>>(bx, partial, nblk, out);
+    diag_final_kernel<<<1, DIAG_THREADS, 0, st>>>(bx, partial, nblk, out);
     return cudaGetLastError();
 }
 

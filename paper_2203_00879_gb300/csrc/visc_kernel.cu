@@ -528,7 +528,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
 // FP32: at most 64 registers, which with 56 KB of shared memory per block
 // keeps four blocks (32 warps) on an SM
 template <typename T>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 4 : 2) visc_rk_kernel(const VArgs<T> a)
+__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 1024 : 512) / (TX * TY)) visc_rk_kernel(const VArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     // blocks whose x and y ranges (with the one-node flux halo) stay off the

@@ -32,6 +32,7 @@ struct BoxRes {
     nopcs_box_desc d{};
     BoxDev dev{};
     LineOpBuf dop64[3], dop32[3], fop[3];
+    LineOpBuf fop32[3];  // mixed form: the filter with FP32 end-row tables
     GemmOpBuf gop[3];  // dense blocks of the FP32 derivative (tensor-core form)
     int sub_n[3] = {0, 0, 0};     // sub-domain length in use per axis (tuned if asked)
     int lines[3] = {0, 0, 0};     // flux-sweep lines per block per axis (0: default)
@@ -162,6 +163,7 @@ void free_box(BoxRes &b)
         b.dop64[a].release();
         b.dop32[a].release();
         b.fop[a].release();
+        b.fop32[a].release();
         b.gop[a].release();
     }
     if (b.Q) cudaFree(b.Q);
@@ -188,6 +190,11 @@ nopcs_status build_axis_ops(nopcs_ctx *ctx, BoxRes &b, int a)
     CK(b.dop64[a].upload(), "operator upload");
     CK(b.dop32[a].upload(), "operator upload");
     CK(b.fop[a].upload(), "operator upload");
+    if (b.mixed) {
+        if (!build_line_op(d.n[a], sn, KIND_FILTER, d.filter_alpha, 1e-8, b.fop32[a].host, msg))
+            return fail(ctx, NOPCS_EINVAL, msg);
+        CK(b.fop32[a].upload(), "operator upload");
+    }
     if (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO) {
         build_dense_blocks(b.dop32[a].host, b.gop[a].host);
         if (gemm_smem_fits(b.gop[a].host)) {
@@ -344,6 +351,7 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     x.g = d.g;
     x.cE = 1.0 / (d.gamma * (d.gamma - 1.0) * d.M * d.M);
     x.dt = d.dt;
+    b.mixed = ctx->prec == NOPCS_MIXED;
 
     for (int a = 0; a < 3; ++a) {
         b.sub_n[a] = d.sub_n[a] == -1 ? 64 : d.sub_n[a];
@@ -400,7 +408,6 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
 
     // state registers and scratch
     const size_t np = (size_t)x.np;
-    b.mixed = ctx->prec == NOPCS_MIXED;
     cudaError_t e = cudaMalloc(&b.Q, (b.mixed ? 5 : 15) * np * sizeof(double));
     if (e != cudaSuccess) {
         b.Q = nullptr;
@@ -551,17 +558,26 @@ cudaError_t enqueue_filter(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
 {
     Timed t(ctx, st, K_FILTER);
     const BoxDev &x = b.dev;
+    if (b.mixed) {
+        // FP32 filter of the deviation D_n (already base-subtracted), x -> y
+        // -> z through the W slab, R and K, then Q_n += F(D_n) - D_n in FP64
+        float *t1 = b.Wm(0), *t2 = b.Rm(), *t3 = b.Km();
+        cudaError_t e = launch_line_filter32(b.fop32[0].dev, 0, x, b.Dn(), t1, st);
+        if (e != cudaSuccess) return e;
+        e = launch_line_filter32(b.fop32[1].dev, 1, x, t1, t2, st);
+        if (e != cudaSuccess) return e;
+        e = launch_line_filter32(b.fop32[2].dev, 2, x, t2, t3, st);
+        if (e != cudaSuccess) return e;
+        return launch_filter_update(x, b.Qn(), t3, b.Wm(0), b.Dn(), st);
+    }
     const int bs = b.d.base_subtract;
-    // two FP64 temporaries: acc and Qs (FP64 form), the two FP32 slabs (mixed form)
-    double *t1 = b.mixed ? (double *)b.W : b.acc();
-    double *t2 = b.mixed ? (double *)b.R : b.Qs();
+    // two FP64 temporaries: acc and Qs
+    double *t1 = b.acc(), *t2 = b.Qs();
     cudaError_t e = launch_line_filter(b.fop[0].dev, 0, x, bs, b.Qn(), t1, st);
     if (e != cudaSuccess) return e;
     e = launch_line_filter(b.fop[1].dev, 1, x, bs, t1, t2, st);
     if (e != cudaSuccess) return e;
-    e = launch_line_filter(b.fop[2].dev, 2, x, bs, t2, b.Qn(), st);
-    if (e != cudaSuccess) return e;
-    return refresh_mixed(b, st);
+    return launch_line_filter(b.fop[2].dev, 2, x, bs, t2, b.Qn(), st);
 }
 
 cudaError_t enqueue_step(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)

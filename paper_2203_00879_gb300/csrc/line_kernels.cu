@@ -161,13 +161,13 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                         val[2] = m * vv + (AXIS == 1 ? pp : T(0));
                         val[3] = m * ww + (AXIS == 2 ? pp : T(0));
                         val[4] = H * ud;
-                    } else {  // FILTER on Q - base
+                    } else {  // FILTER on Q - base (no base tables: the input is a deviation already)
                         const int gk = gsel == 0 ? g : gl;
-                        val[0] = v[u][0] - a.b0[gk];
+                        val[0] = a.b0 ? v[u][0] - a.b0[gk] : v[u][0];
                         val[1] = v[u][1];
                         val[2] = v[u][2];
                         val[3] = v[u][3];
-                        val[4] = v[u][4] - a.b1[gk];
+                        val[4] = a.b1 ? v[u][4] - a.b1[gk] : v[u][4];
                     }
                     if (!STREAM || (g >= org && g <= last)) {
                         T *d = sm + (size_t)(g - org) * LP + l;
@@ -270,11 +270,11 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                         }
                     } else {
                         const int gk = gsel == 0 ? s + rr : gl;
-                        a.out[0][o] = src[0] + a.b0[gk];
+                        a.out[0][o] = a.b0 ? src[0] + a.b0[gk] : src[0];
                         a.out[1][o] = src[fs];
                         a.out[2][o] = src[2 * fs];
                         a.out[3][o] = src[3 * fs];
-                        a.out[4][o] = src[4 * fs] + a.b1[gk];
+                        a.out[4][o] = a.b1 ? src[4 * fs] + a.b1[gk] : src[4 * fs];
                     }
                 }
             }
@@ -356,7 +356,8 @@ cudaError_t init_line_kernels()
         allow_smem<float, MODE_FLUX, 0>(),   allow_smem<float, MODE_FLUX, 1>(),   allow_smem<float, MODE_FLUX, 2>(),
         allow_smem<double, MODE_FLUX, 0>(),  allow_smem<double, MODE_FLUX, 1>(),  allow_smem<double, MODE_FLUX, 2>(),
         allow_smem<double, MODE_FILTER, 0>(), allow_smem<double, MODE_FILTER, 1>(),
-        allow_smem<double, MODE_FILTER, 2>()};
+        allow_smem<double, MODE_FILTER, 2>(),  allow_smem<float, MODE_FILTER, 0>(),
+        allow_smem<float, MODE_FILTER, 1>(),   allow_smem<float, MODE_FILTER, 2>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -411,6 +412,21 @@ cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, 
     a.b0 = bx.rho_b64;
     a.b1 = bx.E_b64;
     return launch_any<double, MODE_FILTER>(op, axis, a, 16, st);
+}
+
+cudaError_t launch_line_filter32(const LineOpDev &op, int axis, const BoxDev &bx, const float *in, float *out,
+                                 cudaStream_t st)
+{
+    LineArgs<float> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
+    for (int k = 0; k < 5; ++k) {
+        a.in[k] = in + (size_t)k * bx.np;
+        a.out[k] = out + (size_t)k * bx.np;
+    }
+    a.ga = bx.ga;
+    a.b0 = nullptr;  // the input is the deviation from the base already
+    a.b1 = nullptr;
+    return launch_any<float, MODE_FILTER>(op, axis, a, 32, st);
 }
 
 template cudaError_t launch_line_field<float>(const LineOpDev &, int, const int *, const float *, float *,

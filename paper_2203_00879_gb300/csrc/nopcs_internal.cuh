@@ -136,6 +136,13 @@ cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], con
 template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
                              int first, cudaStream_t st, int lines = 0);
+// FILTER (FP32, mixed form): out = L(in) on 5 deviation fields (no base).
+cudaError_t launch_line_filter32(const LineOpDev &op, int axis, const BoxDev &bx, const float *in, float *out,
+                                 cudaStream_t st);
+// Mixed-form filter update: Q += (Fd - Dn) per field in FP64 (Fd: the filtered
+// FP32 deviation, Dn: the deviation it was filtered from), then W0 and Dn of
+// the new state.
+cudaError_t launch_filter_update(const BoxDev &bx, double *Q, const float *Fd, float *W, float *Dn, cudaStream_t st);
 // FILTER (FP64): Qout = L(Q - base) + base, 5 fields.
 cudaError_t launch_line_filter(const LineOpDev &op, int axis, const BoxDev &bx, int base_subtract,
                                const double *Qin, double *Qout, cudaStream_t st);

@@ -28,47 +28,82 @@ __device__ __forceinline__ void coords(const BoxDev &bx, long long p, int c[3])
 // rho - rho_b and E - E_b in FP64 and the rest in FP32, using
 // p - p_b = (gamma - 1)(E - E_b - rho |V|^2 / 2) and H - H_b = (E - E_b) + (p - p_b).
 // ---------------------------------------------------------------------------
+// W (and the deviation D_n, mixed form) of one point of the FP64 state
+template <typename T>
+__device__ __forceinline__ void prep_point(const BoxDev &bx, long long p, int kg, double r, double mx, double my,
+                                           double mz, double E, T *__restrict__ W, float *__restrict__ Dn)
+{
+    const long long np = bx.np;
+    if constexpr (sizeof(T) == 8) {
+        const double u = mx / r, v = my / r, w = mz / r;
+        const double pr = (bx.gamma - 1.0) * (E - 0.5 * (mx * u + my * v + mz * w));
+        W[p] = r - bx.rho_b64[kg];
+        W[np + p] = u;
+        W[2 * np + p] = v;
+        W[3 * np + p] = w;
+        W[4 * np + p] = pr - bx.p_b64[kg];
+        W[5 * np + p] = E + pr - bx.H_b64[kg];
+    } else {
+        const float rd = (float)(r - bx.rho_b64[kg]);
+        const float Ed = (float)(E - bx.E_b64[kg]);
+        const float rf = (float)r;
+        const float ir = 1.0f / rf;
+        const float u = (float)mx * ir, v = (float)my * ir, w = (float)mz * ir;
+        const float ke = 0.5f * rf * (u * u + v * v + w * w);
+        const float pd = (float)(bx.gamma - 1.0) * (Ed - ke);
+        W[p] = rd;
+        W[np + p] = u;
+        W[2 * np + p] = v;
+        W[3 * np + p] = w;
+        W[4 * np + p] = pd;
+        W[5 * np + p] = Ed + pd;
+        if (Dn) {  // deviation of the state from the hydrostatic base (mixed form)
+            Dn[p] = rd;
+            Dn[np + p] = (float)mx;
+            Dn[2 * np + p] = (float)my;
+            Dn[3 * np + p] = (float)mz;
+            Dn[4 * np + p] = Ed;
+        }
+    }
+}
+
+// grid-stride over (y, z) rows, threads along x: no 64-bit division per point
 template <typename T>
 __global__ void prep_kernel(const BoxDev bx, const double *__restrict__ Q, T *__restrict__ W,
                             float *__restrict__ Dn)
 {
     const long long np = bx.np;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
-         p += (long long)gridDim.x * blockDim.x) {
-        int c[3];
-        coords(bx, p, c);
-        const int kg = c[bx.ga];
-        const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
-        if constexpr (sizeof(T) == 8) {
-            const double u = mx / r, v = my / r, w = mz / r;
-            const double pr = (bx.gamma - 1.0) * (E - 0.5 * (mx * u + my * v + mz * w));
-            W[p] = r - bx.rho_b64[kg];
-            W[np + p] = u;
-            W[2 * np + p] = v;
-            W[3 * np + p] = w;
-            W[4 * np + p] = pr - bx.p_b64[kg];
-            W[5 * np + p] = E + pr - bx.H_b64[kg];
-        } else {
-            const float rd = (float)(r - bx.rho_b64[kg]);
-            const float Ed = (float)(E - bx.E_b64[kg]);
-            const float rf = (float)r;
-            const float ir = 1.0f / rf;
-            const float u = (float)mx * ir, v = (float)my * ir, w = (float)mz * ir;
-            const float ke = 0.5f * rf * (u * u + v * v + w * w);
-            const float pd = (float)(bx.gamma - 1.0) * (Ed - ke);
-            W[p] = rd;
-            W[np + p] = u;
-            W[2 * np + p] = v;
-            W[3 * np + p] = w;
-            W[4 * np + p] = pd;
-            W[5 * np + p] = Ed + pd;
-            if (Dn) {  // deviation of the state from the hydrostatic base (mixed form)
-                Dn[p] = rd;
-                Dn[np + p] = (float)mx;
-                Dn[2 * np + p] = (float)my;
-                Dn[3 * np + p] = (float)mz;
-                Dn[4 * np + p] = Ed;
+    const int nx = bx.n[0], ny = bx.n[1], rows = bx.n[1] * bx.n[2];
+    for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+        const int y = rw % ny, z = rw / ny;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long p = (long long)rw * nx + x;
+            const int kg = bx.ga == 0 ? x : (bx.ga == 1 ? y : z);
+            prep_point<T>(bx, p, kg, Q[p], Q[np + p], Q[2 * np + p], Q[3 * np + p], Q[4 * np + p], W, Dn);
+        }
+    }
+}
+
+// Mixed-form filter (Sec. 4): the FP32 deviation D_n was filtered into Fd;
+// the state takes the change Fd - D_n in FP64, so its low-order bits survive,
+// and W0 and D_n are recomputed from the new state.
+__global__ void filter_update_kernel(const BoxDev bx, double *__restrict__ Q, const float *__restrict__ Fd,
+                                     float *__restrict__ W, float *__restrict__ Dn)
+{
+    const long long np = bx.np;
+    const int nx = bx.n[0], ny = bx.n[1], rows = bx.n[1] * bx.n[2];
+    for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+        const int y = rw % ny, z = rw / ny;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long p = (long long)rw * nx + x;
+            const int kg = bx.ga == 0 ? x : (bx.ga == 1 ? y : z);
+            double q[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                q[k] = Q[k * np + p] + (double)(Fd[k * np + p] - Dn[k * np + p]);
+                Q[k * np + p] = q[k];
             }
+            prep_point<float>(bx, p, kg, q[0], q[1], q[2], q[3], q[4], W, Dn);
         }
     }
 }
@@ -384,10 +419,22 @@ int grid_for(long long work, int threads)
 
 }  // namespace
 
+static int row_grid(const BoxDev &bx)
+{
+    const int rows = bx.n[1] * bx.n[2];
+    return rows < 152 * 16 ? rows : 152 * 16;
+}
+
 template <typename T>
 cudaError_t launch_prep(const BoxDev &bx, const double *Q, T *W, float *Dn, cudaStream_t st)
 {
-    prep_kernel<T><<<grid_for(bx.np, 256), 256, 0, st>>>(bx, Q, W, Dn);
+    prep_kernel<T><<<row_grid(bx), 256, 0, st>>>(bx, Q, W, Dn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_update(const BoxDev &bx, double *Q, const float *Fd, float *W, float *Dn, cudaStream_t st)
+{
+    filter_update_kernel<<<row_grid(bx), 256, 0, st>>>(bx, Q, Fd, W, Dn);
     return cudaGetLastError();
 }
 

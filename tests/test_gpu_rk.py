@@ -114,6 +114,34 @@ def test_filter_matches_oracle():
             N.nopcs_destroy(ctx)
 
 
+def test_mixed_filter_matches_oracle():
+    """Mixed form: the FP32 filter of the base deviation, applied to the FP64
+    state as Q += F(D) - D, against the oracle's FP64 base-subtracted filter."""
+    N = binding()
+    p = S.box_params((30, 27, 33), sub_n=(8, 16, 0), base_subtract=1, perturb_amp=1e-3, seed=4)
+    ctx = _ctx(N, p, N.NOPCS_MIXED)
+    try:
+        orc = oracle.Solver(p)
+        Q = orc.initial_state()
+        rng = np.random.default_rng(2)
+        Q[0] *= 1 + 1e-4 * rng.standard_normal(Q[0].shape)
+        Q[4] *= 1 + 1e-4 * rng.standard_normal(Q[4].shape)
+        N.nopcs_set_state(ctx, 0, to_dev(Q).data_ptr())
+        N.nopcs_filter(ctx, 0)
+        got = _state(N, ctx, p)
+        ref = orc.filter(Q)
+        err = field_rel(got, ref)
+        assert np.all(err <= 1e-5), err
+        # the filter changed the state by far more than the error
+        assert np.all(field_rel(Q, ref)[1:4] > 100 * err[1:4])
+        # points within three nodes of a wall along every axis are never
+        # filtered: their state keeps its bits
+        assert np.array_equal(got[:, :3, :3, :3], Q[:, :3, :3, :3])
+        assert np.array_equal(got[:, -3:, -3:, -3:], Q[:, -3:, -3:, -3:])
+    finally:
+        N.nopcs_destroy(ctx)
+
+
 def test_diagnostics_match_oracle():
     N = binding()
     p = S.box_params((20, 22, 26), sub_n=(8, 8, 8), perturb_amp=1e-3)

@@ -176,7 +176,8 @@ def run_reference(args):
 def run_deriv_microbench(args):
     """NOHAP first derivative of a seeded 512^3 field (random-phase sines plus
     N(0, 1e-3^2) noise) along x, y, z: Thomas form in FP64 and FP32 and the
-    3xTF32 tensor-core form, sub-domains of 32, 64 and 128.  Each case is timed
+    3xTF32 tensor-core form, sub-domains of 32, 64 and 128, and the banded
+    explicit form (FP32, no sub-domains).  Each case is timed
     with CUDA events over `steps` calls after `warmup`; the field (0.5-1 GB) is
     larger than L2."""
     import torch
@@ -202,7 +203,10 @@ def run_deriv_microbench(args):
     rows = []
     for sub_n in (32, 64, 128):
         p = box(n, sub_n, perturb_amp=0.0)
-        for form_name, form in (("thomas", N.NOPCS_FORM_THOMAS), ("gemm_3xtf32", N.NOPCS_FORM_GEMM_3XTF32)):
+        forms = [("thomas", N.NOPCS_FORM_THOMAS), ("gemm_3xtf32", N.NOPCS_FORM_GEMM_3XTF32)]
+        if sub_n == 64:  # the banded form has no sub-domains: timed once
+            forms.append(("banded", N.NOPCS_FORM_BANDED))
+        for form_name, form in forms:
             try:
                 ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, form=form, stream=st.cuda_stream)
             except N.NopcsError as exc:
@@ -226,7 +230,11 @@ def run_deriv_microbench(args):
                     gbs = 2 * es * n ** 3 / (ms * 1e-3) / 1e9
                     row = {"form": form_name, "dtype": dname, "sub_n": sub_n, "axis": "xyz"[axis], "ms": ms,
                            "points_per_s": n ** 3 / (ms * 1e-3), "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
-                    if form_name != "thomas":
+                    if form_name == "banded":
+                        # 49 FP32 FMAs per point (the interior stencil)
+                        row["sub_n"] = None
+                        row["fp32_tflops"] = 2.0 * 49 * n ** 3 / (ms * 1e-3) / 1e12
+                    elif form_name != "thomas":
                         kpad = (sub_n + 48 + 7) // 8 * 8
                         tflops = 6.0 * kpad * n ** 3 / (ms * 1e-3) / 1e12
                         row.update({"tensor_tflops": tflops, "tensor_frac": tflops / tf32_peak})

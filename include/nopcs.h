@@ -55,12 +55,17 @@ typedef enum {
 } nopcs_precision;
 
 typedef enum {
-    NOPCS_FORM_AUTO = 0,   /* per box and axis, the faster of the two for FP32  */
+    NOPCS_FORM_AUTO = 0,   /* per box and axis, the fastest form for FP32       */
                            /* derivatives, measured at nopcs_init               */
     NOPCS_FORM_THOMAS = 1, /* per-sub-domain Thomas sweeps                      */
     NOPCS_FORM_GEMM_3XTF32 = 2, /* FP32 derivatives on the tensor cores (tcgen05, */
                                 /* split TF32); FP64 ones keep the Thomas form    */
-    NOPCS_FORM_GEMM_BF16X3 = 3  /* declared; returns NOPCS_EUNSUPPORTED          */
+    NOPCS_FORM_GEMM_BF16X3 = 3, /* declared; returns NOPCS_EUNSUPPORTED          */
+    NOPCS_FORM_BANDED = 4  /* FP32 derivatives as the equivalent explicit scheme */
+                           /* (Eq. CS:fpCf_i) at every row: rows of the global  */
+                           /* C = A^-1 B truncated at 1e-8, no Thomas; FP64     */
+                           /* ones keep the Thomas form.  The flux sweeps of    */
+                           /* the RK step use Thomas under every form.          */
 } nopcs_form;
 
 /*
@@ -209,8 +214,8 @@ nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out);
 /*
  * Choices in force for box `box` (caller arrays of 3 ints, any may be NULL):
  * the sub-domain length per axis (the autotuner's pick where the descriptor
- * asked for -1), the form of the FP32 derivative per axis (NOPCS_FORM_THOMAS
- * or NOPCS_FORM_GEMM_3XTF32) and the flux sweeps' tile width per axis (grid
+ * asked for -1), the form of the FP32 derivative per axis (NOPCS_FORM_THOMAS,
+ * NOPCS_FORM_GEMM_3XTF32 or NOPCS_FORM_BANDED) and the flux sweeps' tile width per axis (grid
  * lines per CUDA block; 0 = the precision's default, untuned for small boxes).
  */
 nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form, int *tile_lines);
@@ -254,6 +259,20 @@ nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double alpha_f, dou
  */
 nopcs_status nopcs_operator_apply(int N, int sub_n, int kind, double alpha_f, double thresh, const double *f,
                                   double *g);
+
+/*
+ * Host evaluation of the banded explicit form of the same line operator
+ * (NOPCS_FORM_BANDED): the equivalent explicit scheme g_i = sum_j C_ij f_j of
+ * Sec. 3 (Eqs. CS:fpCf, CS:fpCf_i), applied at every row instead of at the
+ * sub-domain ends only, with the rows of the global C = A^-1 B truncated at
+ * |C| < thresh.  Rows in [*interior_lo, *interior_hi] use one stencil of
+ * offsets -*half_width .. *half_width; the rows near the walls use their own
+ * tabulated windows.  FP64, needs no GPU; f and g are host arrays of N
+ * doubles, g dimensionless as for nopcs_operator_apply.  The three outputs may
+ * be NULL.  Errors: EINVAL.
+ */
+nopcs_status nopcs_band_apply(int N, int kind, double alpha_f, double thresh, const double *f, double *g,
+                              int *half_width, int *interior_lo, int *interior_hi);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,8 @@ struct BoxRes {
     int sub_n[3] = {0, 0, 0};     // sub-domain length in use per axis (tuned if asked)
     int lines[3] = {0, 0, 0};     // flux-sweep lines per block per axis (0: default)
     bool deriv_gemm[3] = {false, false, false};  // FP32 derivative on the tensor cores
+    bool deriv_band[3] = {false, false, false};  // FP32 derivative in the banded explicit form
+    BandBuf bop[3];                              // banded FP32 tables (forms BANDED and AUTO)
     bool mixed = false;
     double *Q = nullptr;
     void *W = nullptr, *R = nullptr;
@@ -165,6 +167,7 @@ void free_box(BoxRes &b)
         b.fop[a].release();
         b.fop32[a].release();
         b.gop[a].release();
+        b.bop[a].release();
     }
     if (b.Q) cudaFree(b.Q);
     if (b.W) cudaFree(b.W);
@@ -194,6 +197,15 @@ nopcs_status build_axis_ops(nopcs_ctx *ctx, BoxRes &b, int a)
         if (!build_line_op(d.n[a], sn, KIND_FILTER, d.filter_alpha, 1e-8, b.fop32[a].host, msg))
             return fail(ctx, NOPCS_EINVAL, msg);
         CK(b.fop32[a].upload(), "operator upload");
+    }
+    if (ctx->form == NOPCS_FORM_BANDED || ctx->form == NOPCS_FORM_AUTO) {
+        b.bop[a].release();
+        if (!build_band_op(d.n[a], KIND_DERIV, 0.0, 1e-8, b.bop[a].host, msg)) return fail(ctx, NOPCS_EINVAL, msg);
+        if (band_supported(b.bop[a].host)) {
+            CK(b.bop[a].upload(), "banded operator upload");
+        } else if (ctx->form == NOPCS_FORM_BANDED) {
+            return fail(ctx, NOPCS_EUNSUPPORTED, "the banded form's tables do not fit its kernel for this line length");
+        }
     }
     if (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO) {
         build_dense_blocks(b.dop32[a].host, b.gop[a].host);
@@ -304,7 +316,8 @@ nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
         CK(cudaMemsetAsync(fin, 0, 2 * (size_t)x.np * sizeof(float), st), "autotune");
         for (int a = 0; a < 3; ++a) {
             b.deriv_gemm[a] = false;
-            if (!b.gop[a].mem) continue;
+            b.deriv_band[a] = false;
+            if (!b.gop[a].mem && !b.bop[a].mem) continue;
             const std::string key = std::string(key0) + ",g" + std::to_string(a) + "," + std::to_string(b.sub_n[a]);
             int choice = -1;
             {
@@ -313,16 +326,21 @@ nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
                 if (it != g_tune_cache.end()) choice = it->second;
             }
             if (choice < 0) {
-                cudaError_t e1, e2;
+                cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
                 const float tt = time_launches(st, [&] { return launch_line_field<float>(b.dop32[a].dev, a, x.n, fin, fout, 1.0, st); }, e1);
-                const float tg = time_launches(st, [&] { return launch_gemm_field(b.gop[a].dev, a, x.n, fin, fout, 1.0, ctx->dev_err, st); }, e2);
+                const float tg = b.gop[a].mem ? time_launches(st, [&] { return launch_gemm_field(b.gop[a].dev, a, x.n, fin, fout, 1.0, ctx->dev_err, st); }, e2) : 1e30f;
+                const float tb = b.bop[a].mem ? time_launches(st, [&] { return launch_band_field(b.bop[a], a, x.n, fin, fout, 1.0, st); }, e3) : 1e30f;
                 if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "autotune");
                 if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "autotune");
-                choice = tg < tt ? 1 : 0;
+                if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "autotune");
+                choice = 0;
+                if (tg < tt && tg <= tb) choice = 1;
+                if (tb < tt && tb < tg) choice = 2;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 g_tune_cache[key] = choice;
             }
             b.deriv_gemm[a] = choice == 1;
+            b.deriv_band[a] = choice == 2;
         }
     }
     return NOPCS_OK;
@@ -356,6 +374,7 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
     for (int a = 0; a < 3; ++a) {
         b.sub_n[a] = d.sub_n[a] == -1 ? 64 : d.sub_n[a];
         b.deriv_gemm[a] = ctx->form == NOPCS_FORM_GEMM_3XTF32;
+        b.deriv_band[a] = ctx->form == NOPCS_FORM_BANDED;
         nopcs_status st = build_axis_ops(ctx, b, a);
         if (st != NOPCS_OK) return st;
     }
@@ -630,7 +649,7 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
     *out = nullptr;
     if (!boxes || nboxes < 1) return fail(nullptr, NOPCS_EINVAL, "need at least one box");
     if (prec != NOPCS_FP64 && prec != NOPCS_MIXED) return fail(nullptr, NOPCS_EINVAL, "bad precision");
-    if (form < NOPCS_FORM_AUTO || form > NOPCS_FORM_GEMM_BF16X3) return fail(nullptr, NOPCS_EINVAL, "bad form");
+    if (form < NOPCS_FORM_AUTO || form > NOPCS_FORM_BANDED) return fail(nullptr, NOPCS_EINVAL, "bad form");
     for (int i = 0; i < nboxes; ++i) {
         std::string m;
         if (!valid_box(boxes[i], m)) return fail(nullptr, NOPCS_EINVAL, "box " + std::to_string(i) + ": " + m);
@@ -764,6 +783,8 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
         if (dtype == 1 && b.deriv_gemm[axis])
             e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)f, (float *)b.scratch, scale,
                                   ctx->dev_err, st);
+        else if (dtype == 1 && b.deriv_band[axis])
+            e = launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)f, (float *)b.scratch, scale, st);
         else if (dtype == 0)
             e = launch_line_field<double>(op, axis, b.dev.n, (const double *)f, (double *)b.scratch, scale, st);
         else
@@ -774,6 +795,8 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
     cudaError_t e;
     if (dtype == 1 && b.deriv_gemm[axis])
         e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)src, (float *)df, scale, ctx->dev_err, st);
+    else if (dtype == 1 && b.deriv_band[axis])
+        e = launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)src, (float *)df, scale, st);
     else if (dtype == 0)
         e = launch_line_field<double>(op, axis, b.dev.n, (const double *)src, (double *)df, scale, st);
     else
@@ -895,7 +918,9 @@ nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form
     const BoxRes &b = ctx->boxes[box];
     for (int a = 0; a < 3; ++a) {
         if (sub_n) sub_n[a] = b.sub_n[a];
-        if (deriv_form) deriv_form[a] = b.deriv_gemm[a] ? NOPCS_FORM_GEMM_3XTF32 : NOPCS_FORM_THOMAS;
+        if (deriv_form)
+            deriv_form[a] = b.deriv_gemm[a] ? NOPCS_FORM_GEMM_3XTF32
+                                            : (b.deriv_band[a] ? NOPCS_FORM_BANDED : NOPCS_FORM_THOMAS);
         if (tile_lines) tile_lines[a] = b.lines[a];
     }
     return NOPCS_OK;

@@ -40,6 +40,38 @@ struct LineOpHost {
     int kconv64 = 0, kconv32 = 0; // factors of rows >= kconv equal the limit in that precision
 };
 
+// Banded explicit form of a line operator (all rows of the truncated global C).
+struct BandHost {
+    int N = 0, kind = 0;
+    int h = 0;                   // interior half-width: taps at offsets -h .. h
+    int in_lo = 0, in_hi = -1;   // rows in_lo .. in_hi use the interior stencil
+    std::vector<double> stencil; // 2h + 1 taps
+    int W = 0;                   // longest window of a tabulated row
+    std::vector<int> wrow, wj0, wlen;  // tabulated rows, first column and length of their windows
+    std::vector<double> wtap;    // W slots per tabulated row (taps, then zeros)
+};
+bool build_band_op(int N, int kind, double alpha_f, double thresh, BandHost &bh, std::string &msg);
+void apply_band_host(const BandHost &bh, const double *f, double *g);
+// Device copy of the FP32 banded tables (band_kernels.cu).
+struct BandDev {
+    const float *cg = nullptr;    // interior stencil, centred in the kernel's tap count
+    const int *wj0 = nullptr;     // tabulated rows: first column of the window
+    const int *wlen = nullptr;    // tabulated rows: window length
+    const float *wtap = nullptr;  // tabulated rows: taps
+};
+struct BandBuf {
+    BandHost host;
+    BandDev dev;
+    void *mem = nullptr;
+    cudaError_t upload();
+    void release();
+};
+// the FP32 band kernel handles the table (stencil width, window placement)
+bool band_supported(const BandHost &h);
+// out = scale * C_band f along `axis` (FP32)
+cudaError_t launch_band_field(const BandBuf &op, int axis, const int n[3], const float *f, float *out, double scale,
+                              cudaStream_t st);
+
 // Device view passed by value to the line kernels.
 struct LineOpDev {
     int N, nsub, nexp, maxm, max_tile, max_taps, max_win;

@@ -84,6 +84,62 @@ void solve_At(const LineOpHost &op, int i, std::vector<double> &y)
     for (int r = N - 2; r >= 0; --r) y[r] = (d[r] - up[r] * y[r + 1]) / di[r];
 }
 
+// banded B of the global system: explicit closure rows, then the interior
+// right-hand side (antisymmetric for the derivative, symmetric for the filter)
+void fill_B(const LineOpHost &op, Banded &B)
+{
+    const int N = op.N;
+    auto setB = [&](int r, int c, double v) {
+        int k = c - B.c0[r];
+        B.w[(size_t)r * 7 + k] = v;
+    };
+    for (int r = 0; r < N; ++r) {
+        if (r < op.nexp) {
+            B.c0[r] = 0;
+            for (int j = 0; j < 5 && j < N; ++j) setB(r, j, op.ex[r][j]);
+        } else if (r > N - 1 - op.nexp) {
+            int rr = N - 1 - r;
+            B.c0[r] = N - 7 < 0 ? 0 : N - 7;
+            for (int j = 0; j < 5; ++j)
+                if (op.ex[rr][j] != 0.0) setB(r, N - 1 - j, op.ex_sign * op.ex[rr][j]);
+        } else {
+            B.c0[r] = r - 3;
+            if (op.kind == KIND_DERIV) {
+                setB(r, r - 2, -op.rb[1]);
+                setB(r, r - 1, -op.rb[0]);
+                setB(r, r + 1, op.rb[0]);
+                setB(r, r + 2, op.rb[1]);
+            } else {
+                setB(r, r, op.rb[0]);
+                for (int k = 1; k <= 3; ++k) {
+                    setB(r, r - k, op.rb[k]);
+                    setB(r, r + k, op.rb[k]);
+                }
+            }
+        }
+    }
+}
+
+// row i of the global C = A^-1 B (dense, length N): explicit rows are their
+// own B rows; implicit rows are y^T B with A^T y = e_i
+void global_C_row(const LineOpHost &op, const Banded &B, int i, std::vector<double> &y, std::vector<double> &crow)
+{
+    const int N = op.N;
+    crow.assign(N, 0.0);
+    if (is_explicit(op, i)) {
+        for (int j = 0; j < N; ++j) crow[j] = B.at(i, j);
+        return;
+    }
+    solve_At(op, i, y);
+    for (int r = 0; r < N; ++r) {
+        if (y[r] == 0.0) continue;
+        for (int k = 0; k < 7; ++k) {
+            int c = B.c0[r] + k;
+            if (c >= 0 && c < N) crow[c] += y[r] * B.w[(size_t)r * 7 + k];
+        }
+    }
+}
+
 }  // namespace
 
 bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, LineOpHost &op,
@@ -110,10 +166,6 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
     B.N = N;
     B.c0.assign(N, 0);
     B.w.assign((size_t)N * 7, 0.0);
-    auto setB = [&](int r, int c, double v) {
-        int k = c - B.c0[r];
-        B.w[(size_t)r * 7 + k] = v;
-    };
     int w;  // half-width of the interior right-hand side
     if (kind == KIND_DERIV) {
         op.nexp = 2;
@@ -144,32 +196,7 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
         for (int r = 0; r < 3; ++r) op.ex[r][r] = 1.0;
         op.ex_sign = 1.0;
     }
-    // banded B
-    for (int r = 0; r < N; ++r) {
-        if (r < op.nexp) {
-            B.c0[r] = 0;
-            for (int j = 0; j < 5 && j < N; ++j) setB(r, j, op.ex[r][j]);
-        } else if (r > N - 1 - op.nexp) {
-            int rr = N - 1 - r;
-            B.c0[r] = N - 7 < 0 ? 0 : N - 7;
-            for (int j = 0; j < 5; ++j)
-                if (op.ex[rr][j] != 0.0) setB(r, N - 1 - j, op.ex_sign * op.ex[rr][j]);
-        } else {
-            B.c0[r] = r - 3;
-            if (kind == KIND_DERIV) {
-                setB(r, r - 2, -op.rb[1]);
-                setB(r, r - 1, -op.rb[0]);
-                setB(r, r + 1, op.rb[0]);
-                setB(r, r + 2, op.rb[1]);
-            } else {
-                setB(r, r, op.rb[0]);
-                for (int k = 1; k <= 3; ++k) {
-                    setB(r, r - k, op.rb[k]);
-                    setB(r, r + k, op.rb[k]);
-                }
-            }
-        }
-    }
+    fill_B(op, B);
     // partition and end rows
     std::vector<int> start(N + 2);
     op.nsub = partition_rule(N, sub_n, start.data());
@@ -460,9 +487,120 @@ void LineOpBuf::release()
     mem = nullptr;
 }
 
+
+
+// Banded explicit form (the equivalent explicit scheme applied at every row):
+// all rows of the global C = A^-1 B, truncated at thresh.  Rows far enough
+// from both walls equal one translation-invariant stencil (to within thresh);
+// the rest are tabulated with their own windows.
+bool build_band_op(int N, int kind, double alpha_f, double thresh, BandHost &bh, std::string &msg)
+{
+    LineOpHost op;
+    if (!build_line_op(N, 0, kind, alpha_f, thresh, op, msg)) return false;
+    Banded B;
+    B.N = N;
+    B.c0.assign(N, 0);
+    B.w.assign((size_t)N * 7, 0.0);
+    fill_B(op, B);
+    std::vector<std::vector<double>> C(N);
+    std::vector<double> y;
+    std::vector<int> lo(N), hi(N);
+    for (int i = 0; i < N; ++i) {
+        global_C_row(op, B, i, y, C[i]);
+        lo[i] = N;
+        hi[i] = -1;
+        for (int j = 0; j < N; ++j) {
+            if (fabs(C[i][j]) < thresh) {
+                C[i][j] = 0.0;
+            } else {
+                lo[i] = j < lo[i] ? j : lo[i];
+                hi[i] = j;
+            }
+        }
+        if (hi[i] < lo[i]) lo[i] = hi[i] = i;
+    }
+    bh = BandHost();
+    bh.N = N;
+    bh.kind = kind;
+    // interior stencil from the middle row
+    const int im = N / 2;
+    int h = im - lo[im] > hi[im] - im ? im - lo[im] : hi[im] - im;
+    bh.h = h;
+    bh.stencil.assign(2 * h + 1, 0.0);
+    for (int k = -h; k <= h; ++k)
+        if (im + k >= 0 && im + k < N) bh.stencil[k + h] = C[im][im + k];
+    auto matches = [&](int i) {
+        if (i - h < 0 || i + h > N - 1 || lo[i] < i - h || hi[i] > i + h) return false;
+        for (int k = -h; k <= h; ++k)
+            if (fabs(C[i][i + k] - bh.stencil[k + h]) > thresh) return false;
+        return true;
+    };
+    // the interior run around the middle row
+    int a = im, b = im;
+    if (matches(im)) {
+        while (a - 1 >= 0 && matches(a - 1)) --a;
+        while (b + 1 < N && matches(b + 1)) ++b;
+        bh.in_lo = a;
+        bh.in_hi = b;
+    } else {
+        bh.in_lo = N;  // no interior rows: every row is tabulated
+        bh.in_hi = N - 1;
+    }
+    // tabulated rows: 0 .. in_lo-1 and in_hi+1 .. N-1
+    int W = 1;
+    for (int i = 0; i < N; ++i)
+        if (i < bh.in_lo || i > bh.in_hi) W = hi[i] - lo[i] + 1 > W ? hi[i] - lo[i] + 1 : W;
+    bh.W = W;
+    bh.wrow.clear();
+    bh.wj0.clear();
+    bh.wlen.clear();
+    bh.wtap.clear();
+    for (int i = 0; i < N; ++i) {
+        if (i >= bh.in_lo && i <= bh.in_hi) continue;
+        bh.wrow.push_back(i);
+        bh.wj0.push_back(lo[i]);
+        bh.wlen.push_back(hi[i] - lo[i] + 1);
+        for (int k = 0; k < W; ++k) bh.wtap.push_back(lo[i] + k <= hi[i] ? C[i][lo[i] + k] : 0.0);
+    }
+    return true;
+}
+
+// out = C_band f on one line (host, FP64 taps): the banded form's arithmetic
+// in the order the kernel sums it (interior stencil from -h to h, tabulated
+// rows over their windows)
+void apply_band_host(const BandHost &bh, const double *f, double *g)
+{
+    const int N = bh.N, h = bh.h;
+    for (int i = bh.in_lo; i <= bh.in_hi && i < N; ++i) {
+        double acc = 0.0;
+        for (int k = -h; k <= h; ++k) acc += bh.stencil[k + h] * f[i + k];
+        g[i] = acc;
+    }
+    for (size_t t = 0; t < bh.wrow.size(); ++t) {
+        double acc = 0.0;
+        for (int k = 0; k < bh.wlen[t]; ++k) acc += bh.wtap[t * bh.W + k] * f[bh.wj0[t] + k];
+        g[bh.wrow[t]] = acc;
+    }
+}
+
 }  // namespace nopcs
 
 using namespace nopcs;
+
+extern "C" nopcs_status nopcs_band_apply(int N, int kind, double alpha_f, double thresh, const double *f, double *g,
+                                         int *half_width, int *interior_lo, int *interior_hi)
+{
+    if (kind != KIND_DERIV && kind != KIND_FILTER) return NOPCS_EINVAL;
+    if (!f || !g) return NOPCS_EINVAL;
+    BandHost bh;
+    std::string msg;
+    if (!build_band_op(N, kind, alpha_f, thresh, bh, msg)) return NOPCS_EINVAL;
+    apply_band_host(bh, f, g);
+    if (half_width) *half_width = bh.h;
+    if (interior_lo) *interior_lo = bh.in_lo;
+    if (interior_hi) *interior_hi = bh.in_hi;
+    return NOPCS_OK;
+}
 
 extern "C" nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double alpha_f, double thresh,
                                             int *nsub, int *starts, int *end_j0, int *end_len,

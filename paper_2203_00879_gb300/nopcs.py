@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libnopcs.so")
 NOPCS_OK, NOPCS_EINVAL, NOPCS_ENOMEM, NOPCS_ECUDA, NOPCS_EUNSTABLE, NOPCS_ETIMEOUT, NOPCS_EUNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "EUNSUPPORTED"]
 NOPCS_FP64, NOPCS_MIXED = 0, 1
-NOPCS_FORM_AUTO, NOPCS_FORM_THOMAS, NOPCS_FORM_GEMM_3XTF32, NOPCS_FORM_GEMM_BF16X3 = range(4)
+NOPCS_FORM_AUTO, NOPCS_FORM_THOMAS, NOPCS_FORM_GEMM_3XTF32, NOPCS_FORM_GEMM_BF16X3, NOPCS_FORM_BANDED = range(5)
 NOPCS_NUM_KERNELS = 8
 
 
@@ -70,7 +70,8 @@ _L.nopcs_kernel_name.restype = C.c_char_p
 _L.nopcs_operator_rows.argtypes = [_i, _i, _i, _d, _d, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
                                    C.POINTER(_i), C.POINTER(_d), _i]
 _L.nopcs_operator_apply.argtypes = [_i, _i, _i, _d, _d, C.c_void_p, C.c_void_p]
-for _name in ("nopcs_operator_apply", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
+_L.nopcs_band_apply.argtypes = [_i, _i, _d, _d, C.c_void_p, C.c_void_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]
+for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
               "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows", "nopcs_box_info"):
@@ -211,6 +212,20 @@ def nopcs_operator_rows(N: int, sub_n: int, kind: int = 0, alpha_f: float = 0.13
         rows.append((j0[k], [coef[off + t] for t in range(L)]))
         off += L
     return list(starts[: nb + 1]), rows
+
+
+def nopcs_band_apply(N: int, f, kind: int = 0, alpha_f: float = 0.135, thresh: float = 1e-16):
+    """Host FP64 evaluation of the banded explicit form on a numpy line f;
+    returns (g, half_width, interior_lo, interior_hi)."""
+    import numpy as np
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.zeros_like(f)
+    h, lo, hi = _i(), _i(), _i()
+    st = _L.nopcs_band_apply(N, kind, alpha_f, thresh, f.ctypes.data, g.ctypes.data, C.byref(h), C.byref(lo),
+                             C.byref(hi))
+    if st != NOPCS_OK:
+        raise NopcsError(st, "bad operator request")
+    return g, h.value, lo.value, hi.value
 
 
 def nopcs_operator_apply(N: int, sub_n: int, f, kind: int = 0, alpha_f: float = 0.135, thresh: float = 1e-16):

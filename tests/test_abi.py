@@ -106,3 +106,37 @@ def test_host_line_algorithm_matches_oracle(N, Nn, sub_n, kind):
     g = N.nopcs_operator_apply(Nn, sub_n, f, kind=kind)
     ref = oracle.Op(Nn, kind=kind, sub_n=sub_n).nopcs(f)
     assert np.max(np.abs(g - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("Nn", [5, 9, 40, 64, 129, 512])
+@pytest.mark.parametrize("kind,thresh", [(0, 1e-16), (0, 1e-8), (1, 1e-16)])
+def test_band_form_matches_oracle(N, Nn, kind, thresh):
+    """The banded explicit form (every row from the truncated global C) equals
+    the oracle's NOHAP evaluation to within the truncation."""
+    rng = np.random.default_rng(Nn + kind)
+    f = rng.standard_normal(Nn)
+    g, h, lo, hi = N.nopcs_band_apply(Nn, f, kind=kind, thresh=thresh)
+    ref = oracle.Op(Nn, kind=kind, sub_n=0).nopcs(f)
+    tol = 1e-14 if thresh < 1e-12 else 2e-7
+    assert np.max(np.abs(g - ref)) <= tol * max(1.0, np.max(np.abs(ref)))
+    if Nn >= 129:
+        # one interior stencil for all rows away from the walls
+        assert lo <= 60 and hi >= Nn - 61 and h == (24 if thresh == 1e-8 else h)
+
+
+def test_band_fp32_stencil_is_the_appendix_row(N):
+    """The interior stencil at the FP32 threshold is the printed equivalent
+    explicit row (Appendix table), 24 taps each side."""
+    Nn = 256
+    f = np.zeros(Nn)
+    k = np.loadtxt(os.path.join(ROOT, "tests", "golden", "oucs3_equivalent_explicit_row.txt"))
+    _, h, lo, hi = N.nopcs_band_apply(Nn, f, kind=0, thresh=1e-8)
+    assert h == 24
+    # apply to unit vectors at an interior row to read the stencil back
+    i = Nn // 2
+    taps = []
+    for j in range(i - h, i + h + 1):
+        e = np.zeros(Nn)
+        e[j] = 1.0
+        taps.append(N.nopcs_band_apply(Nn, e, kind=0, thresh=1e-8)[0][i])
+    assert np.max(np.abs(np.array(taps) - k[24:73, 1])) < 2e-16

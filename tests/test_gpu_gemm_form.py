@@ -74,7 +74,8 @@ def test_autotuner_choices_and_parity():
     try:
         info = N.nopcs_box_info(ctx, 0)
         assert all(sn in (32, 64, 128) for sn in info["sub_n"]), info
-        assert all(fm in (N.NOPCS_FORM_THOMAS, N.NOPCS_FORM_GEMM_3XTF32) for fm in info["deriv_form"]), info
+        assert all(fm in (N.NOPCS_FORM_THOMAS, N.NOPCS_FORM_GEMM_3XTF32, N.NOPCS_FORM_BANDED)
+                   for fm in info["deriv_form"]), info
         f = S.sine_field(n, kmax=16, seed=5, noise=1e-3)
         fd = to_dev(f, np.float32)
         out = torch.empty_like(fd)

@@ -79,6 +79,8 @@ def lib():
         L.orc_solver_step.restype = C.c_longlong
         L.orc_solver_set_step.argtypes = [C.c_void_p, C.c_longlong]
         L.orc_diagnostics.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_plane_fields.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, C.c_int, _dp]
+        L.orc_plane_fields.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -238,3 +240,16 @@ class Solver:
         lib().orc_diagnostics(self._s, Q, out)
         return dict(mass=out[0], momentum=out[1:4].copy(), energy_total=out[4], max_speed=out[5],
                     max_dp=out[6], max_mach=out[7], nonfinite=int(out[8]))
+
+    def plane_fields(self, Q, axis: int, index: int, what: int):
+        """Disturbance pressure (what = 0, shape (nb, na)) or the nine
+        vorticity-transport terms of Eq. eqn12_1 (what = 1, shape (9, nb, na))
+        on the plane normal to `axis` at node `index`."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        n = self.p["n"]
+        a, b = [d for d in range(3) if d != axis]
+        out = np.zeros((9 if what else 1, n[b], n[a]))
+        k = lib().orc_plane_fields(self._s, Q, axis, index, what, out)
+        if k < 0:
+            raise ValueError("bad plane request")
+        return out[0] if what == 0 else out

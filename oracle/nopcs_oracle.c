@@ -17,8 +17,10 @@
  *     Eqs. ge1-ge8a, ge12-ge20, reg, bv1-bv3), second-order explicit viscous
  *     terms, classical four-stage RK4 and the implicit filter with coefficient
  *     0.135 applied every 50 steps (Sec. 4, first paragraph);
- *   - the hydrostatic two-temperature initial state (Sec. 2) and the
- *     diagnostics (disturbance pressure, Sec. 4).
+ *   - the hydrostatic two-temperature initial state (Sec. 2), the
+ *     diagnostics (disturbance pressure, Sec. 4) and the plane diagnostics of
+ *     Sec. 4 (disturbance pressure planes and lines, the three right-hand-side
+ *     terms of the vorticity transport equation, Eq. eqn12_1).
  *
  * Only the test suite, the smoke check and the CPU-baseline leg of the
  * benchmark may load this file's library.  It shares no code, header, table or
@@ -778,6 +780,81 @@ void orc_diagnostics(const orc_solver *s, const double *Q, double *out)
     out[6] = dpmax;
     out[7] = mach;
     out[8] = bad;
+}
+
+/*
+ * Paper diagnostics on one plane (Sec. 4).
+ *   what = 0: the disturbance pressure p - p_h (the field of Figs. 4-6);
+ *   what = 1: the three right-hand-side terms of the inviscid vorticity
+ *             transport equation, Eq. eqn12_1 (Fig. 8): vortex stretching
+ *             (omega . grad) V, dilatation -omega (div V) and the baroclinic
+ *             term (grad rho x grad p) / rho^2, each a 3-vector: 9 fields in
+ *             that order, x y z components.
+ * omega = curl V.  Every gradient is the second-order explicit difference of
+ * the viscous terms (central inside, one-sided (-3, 4, -1)/(2h) on a wall);
+ * the paper does not say how it evaluated these terms.  The plane is normal
+ * to `axis` at node `index`; out holds the fields one after another, each
+ * over the two other axes a < b with a fastest.  Returns the number of fields
+ * written, or -1 for a bad request.
+ */
+int orc_plane_fields(orc_solver *s, const double *Q, int axis, int index, int what, double *out)
+{
+    const orc_box *bx = &s->bx;
+    const int nx = bx->n[0], ny = bx->n[1], nz = bx->n[2];
+    if (axis < 0 || axis > 2 || index < 0 || index >= bx->n[axis] || (what != 0 && what != 1)) return -1;
+    const long long np = s->np;
+    const int ia = axis == 0 ? 1 : 0, ib = axis == 2 ? 1 : 2;  /* in-plane axes, a < b */
+    const int na = bx->n[ia], nb = bx->n[ib];
+    const double gam = bx->gamma;
+    /* primitives rho, u, v, w, p over the box */
+    double *prim = s->work;            /* 5 np */
+    double *grad = s->work + 5 * np;   /* 15 np: d(prim q)/d(axis d) at grad + (3 q + d) np */
+    for (long long p = 0; p < np; ++p) {
+        double r = Q[p];
+        double u = Q[np + p] / r, v = Q[2 * np + p] / r, w = Q[3 * np + p] / r;
+        double E = Q[4 * np + p];
+        prim[p] = r;
+        prim[np + p] = u;
+        prim[2 * np + p] = v;
+        prim[3 * np + p] = w;
+        prim[4 * np + p] = (gam - 1.0) * (E - 0.5 * r * (u * u + v * v + w * w));
+    }
+    if (what == 1)
+        for (int q = 0; q < 5; ++q)
+            for (int d = 0; d < 3; ++d) orc_d2_axis(nx, ny, nz, d, s->h[d], prim + q * np, grad + (3 * q + d) * np);
+    const long long plane = (long long)na * nb;
+    for (int jb = 0; jb < nb; ++jb)
+        for (int ja = 0; ja < na; ++ja) {
+            int c[3];
+            c[axis] = index;
+            c[ia] = ja;
+            c[ib] = jb;
+            long long p = c[0] + (long long)nx * (c[1] + (long long)ny * c[2]);
+            long long o = (long long)jb * na + ja;
+            if (what == 0) {
+                out[o] = prim[4 * np + p] - s->p_h[c[bx->gravity_axis]];
+                continue;
+            }
+            /* G[i][j] = d V_i / d x_j */
+            double G[3][3], dr[3], dpr[3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) G[i][j] = grad[(3 * (1 + i) + j) * np + p];
+            for (int j = 0; j < 3; ++j) {
+                dr[j] = grad[(3 * 0 + j) * np + p];
+                dpr[j] = grad[(3 * 4 + j) * np + p];
+            }
+            double om[3] = {G[2][1] - G[1][2], G[0][2] - G[2][0], G[1][0] - G[0][1]};
+            double divv = G[0][0] + G[1][1] + G[2][2];
+            double r = prim[p], ir2 = 1.0 / (r * r);
+            double cr[3] = {dr[1] * dpr[2] - dr[2] * dpr[1], dr[2] * dpr[0] - dr[0] * dpr[2],
+                            dr[0] * dpr[1] - dr[1] * dpr[0]};
+            for (int i = 0; i < 3; ++i) {
+                out[(0 + i) * plane + o] = om[0] * G[i][0] + om[1] * G[i][1] + om[2] * G[i][2];
+                out[(3 + i) * plane + o] = -om[i] * divv;
+                out[(6 + i) * plane + o] = cr[i] * ir2;
+            }
+        }
+    return what == 0 ? 1 : 9;
 }
 
 int orc_num_threads(void)

@@ -212,6 +212,24 @@ nopcs_status nopcs_filter(nopcs_ctx *ctx, int box);
 nopcs_status nopcs_diagnostics(nopcs_ctx *ctx, int box, nopcs_diag *out);
 
 /*
+ * Plane diagnostics of Sec. 4 from box `box`'s current FP64 state, on the
+ * plane normal to `axis` (0, 1, 2) at node `index`:
+ *   what = NOPCS_PLANE_DP (0): the disturbance pressure p - p_h, 1 field;
+ *   what = NOPCS_PLANE_VORTICITY_TERMS (1): the three right-hand-side terms
+ *     of the inviscid vorticity transport equation (Eq. eqn12_1) -- vortex
+ *     stretching (omega . grad) V, dilatation -omega (div V) and the
+ *     baroclinic term (grad rho x grad p) / rho^2 -- x, y, z components each,
+ *     9 fields in that order; omega = curl V and every gradient is the
+ *     second-order explicit difference of the viscous terms (central inside,
+ *     one-sided on a wall).
+ * out: caller-owned device array of nfields x n_b x n_a doubles, where a < b
+ * are the two other axes and a runs fastest.  Enqueued on the context stream
+ * (nopcs_synchronize waits).  Errors: EINVAL for a bad axis, index or `what`.
+ */
+enum { NOPCS_PLANE_DP = 0, NOPCS_PLANE_VORTICITY_TERMS = 1 };
+nopcs_status nopcs_plane_fields(nopcs_ctx *ctx, int box, int axis, int index, int what, double *out);
+
+/*
  * Choices in force for box `box` (caller arrays of 3 ints, any may be NULL):
  * the sub-domain length per axis (the autotuner's pick where the descriptor
  * asked for -1), the form of the FP32 derivative per axis (NOPCS_FORM_THOMAS,

@@ -67,7 +67,7 @@ KERNEL_FILES = {
     "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu"], "diagnostics": ["rk_kernels.cu"],
     "sweep_x": ["line_kernels.cu", "line_solve.cuh"], "sweep_y": ["line_kernels.cu", "line_solve.cuh"],
     "sweep_z": ["line_kernels.cu", "line_solve.cuh"],
-    "filter": ["line_kernels.cu", "line_solve.cuh"], "visc_rk_update": ["visc_kernel.cu"],
+    "filter": ["line_kernels.cu", "line_solve.cuh", "rk_kernels.cu"], "visc_rk_update": ["visc_kernel.cu"],
 }
 
 

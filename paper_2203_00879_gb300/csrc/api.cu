@@ -926,6 +926,20 @@ nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form
     return NOPCS_OK;
 }
 
+nopcs_status nopcs_plane_fields(nopcs_ctx *ctx, int box, int axis, int index, int what, double *out)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (axis < 0 || axis > 2) return fail(ctx, NOPCS_EINVAL, "axis must be 0, 1 or 2");
+    BoxRes &b = ctx->boxes[box];
+    if (index < 0 || index >= b.dev.n[axis]) return fail(ctx, NOPCS_EINVAL, "plane index out of range");
+    if (what != NOPCS_PLANE_DP && what != NOPCS_PLANE_VORTICITY_TERMS)
+        return fail(ctx, NOPCS_EINVAL, "what must be NOPCS_PLANE_DP or NOPCS_PLANE_VORTICITY_TERMS");
+    if (!out) return fail(ctx, NOPCS_EINVAL, "out is NULL");
+    CK(launch_plane_fields(b.dev, b.Qn(), axis, index, what, out, ctx->stream), "plane fields");
+    return NOPCS_OK;
+}
+
 nopcs_status nopcs_synchronize(nopcs_ctx *ctx)
 {
     if (!ctx) return NOPCS_EINVAL;

@@ -168,6 +168,10 @@ cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], con
 template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
                              int first, cudaStream_t st, int lines = 0);
+// Plane diagnostics (plane_kernels.cu): what 0 disturbance pressure, 1 the
+// nine vorticity-transport terms.
+cudaError_t launch_plane_fields(const BoxDev &bx, const double *Q, int axis, int index, int what, double *out,
+                                cudaStream_t st);
 // FILTER (FP32, mixed form): out = L(in) on 5 deviation fields (no base).
 cudaError_t launch_line_filter32(const LineOpDev &op, int axis, const BoxDev &bx, const float *in, float *out,
                                  cudaStream_t st);

@@ -70,8 +70,9 @@ _L.nopcs_kernel_name.restype = C.c_char_p
 _L.nopcs_operator_rows.argtypes = [_i, _i, _i, _d, _d, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
                                    C.POINTER(_i), C.POINTER(_d), _i]
 _L.nopcs_operator_apply.argtypes = [_i, _i, _i, _d, _d, C.c_void_p, C.c_void_p]
+_L.nopcs_plane_fields.argtypes = [_vp, _i, _i, _i, _i, _vp]
 _L.nopcs_band_apply.argtypes = [_i, _i, _d, _d, C.c_void_p, C.c_void_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]
-for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
+for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_plane_fields", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
               "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows", "nopcs_box_info"):
@@ -171,6 +172,15 @@ def nopcs_box_info(ctx, box: int) -> dict:
     lines = (_i * 3)()
     _check(ctx, _L.nopcs_box_info(ctx, box, sub, form, lines))
     return {"sub_n": list(sub), "deriv_form": list(form), "tile_lines": list(lines)}
+
+
+NOPCS_PLANE_DP, NOPCS_PLANE_VORTICITY_TERMS = 0, 1
+
+
+def nopcs_plane_fields(ctx, box: int, axis: int, index: int, what: int, out_ptr: int) -> None:
+    """Plane diagnostics (disturbance pressure or the nine vorticity-transport
+    terms) into a caller-owned device buffer; enqueued on the context stream."""
+    _check(ctx, _L.nopcs_plane_fields(ctx, box, axis, index, what, out_ptr))
 
 
 def nopcs_synchronize(ctx) -> None:

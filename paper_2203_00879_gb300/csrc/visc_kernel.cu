@@ -390,18 +390,10 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
                 FV[(k * FH + ty + 1) * TX + tx] = F[k];
             }
         }
-        if (threadIdx.x < 2 * TY) {  // E_v on the x halo
-            const int side = threadIdx.x / TY, hy = threadIdx.x % TY;
-            const int lx = side ? TX : -1;
-            const int gx = rg.x0 + lx, gy = rg.y0 + hy;
-            if (gx >= 0 && gx < nx && gy < ny) {
-                T E[4], F[4];
-                flux_xy(a, stencil_at(lx, hy, 0, o), true, false, E, F);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) EV[(k * TY + hy) * EW + lx + 1] = E[k];
-            }
-        } else if (threadIdx.x < 2 * TY + 2 * TX) {  // F_v on the y halo
-            const int t = threadIdx.x - 2 * TY;
+        // halo fluxes: F_v on the y halo in warps 0-1, E_v on the x halo in
+        // warp 2, so no warp evaluates more than one halo flux per plane
+        if (threadIdx.x < 2 * TX) {  // F_v on the y halo
+            const int t = threadIdx.x;
             const int side = t / TX, hx = t % TX;
             const int ly = side ? TY : -1;
             const int gx = rg.x0 + hx, gy = rg.y0 + ly;
@@ -410,6 +402,17 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
                 flux_xy(a, stencil_at(hx, ly, 0, o), false, true, E, F);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) FV[(k * FH + ly + 1) * TX + hx] = F[k];
+            }
+        } else if (threadIdx.x < 2 * TX + 2 * TY) {  // E_v on the x halo
+            const int t = threadIdx.x - 2 * TX;
+            const int side = t / TY, hy = t % TY;
+            const int lx = side ? TX : -1;
+            const int gx = rg.x0 + lx, gy = rg.y0 + hy;
+            if (gx >= 0 && gx < nx && gy < ny) {
+                T E[4], F[4];
+                flux_xy(a, stencil_at(lx, hy, 0, o), true, false, E, F);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) EV[(k * TY + hy) * EW + lx + 1] = E[k];
             }
         }
         // G_v planes the z divergence of plane o needs: o-1 and o+1, or

@@ -1,23 +1,23 @@
 // NOHAP line sweeps on sm_103a (arXiv 2203.00879, Sec. 3).
 //
 // One CUDA block owns one sub-domain [s, e] of LINES neighbouring grid lines.
-// It stages the rows the sub-domain needs (its own points, the end-row
-// supports of up to 48 (FP64) / 24 (FP32) points into the neighbouring
-// sub-domains, and the +-2 (+-3 for the filter) right-hand-side stencil) in
+// It streams in the rows the sub-domain needs: its own points, the +-2 (+-3
+// for the filter) right-hand-side stencil, and the end-row supports of up to
+// 48 (FP64) / 24 (FP32) points into the neighbouring sub-domains.  As rows
+// pass, the two end values g_i = sum_j C_ij f_j (Eq. CS:fpCf_i) are summed
+// from them; only the solve window (the own rows plus the stencil) is kept in
 // shared memory, laid out [field][row][line] with an odd line pitch, so that
-//   - a line along the contiguous x axis is read row-contiguous (coalesced)
-//     and transposed on the fly into the [row][line] layout, and
+//   - a line along the contiguous x axis is read row-contiguous (coalesced,
+//     a warp per line, its lanes' partial sums reduced with shuffles) and
+//     transposed on the fly into the [row][line] layout, and
 //   - lines along y or z are read line-contiguous (coalesced along x).
-// Each thread then owns one (line, field) column and
-//   1. evaluates the two sub-domain end values with the equivalent explicit
-//      rows g_i = sum_j C_ij f_j (Eq. CS:fpCf_i) and any explicit wall-closure
-//      row inside the sub-domain,
-//   2. runs the Thomas forward sweep over the implicit rows (tabulated factors,
-//      the end values moved to the right-hand side) keeping the last 2W+1
-//      inputs in registers and writing the forward values in place,
-//   3. back-substitutes in place.
-// The block finally writes its own rows back (transposed again for x).
-// Sub-domains are independent, so no block waits for another.
+// Each thread then owns one (line, field) column and solves it
+// (line_solve.cuh): explicit wall-closure rows, a Thomas forward sweep over
+// the implicit rows with the end values moved to the right-hand side, and
+// back substitution, in place.  The block finally writes its own rows back
+// (transposed again for x).  Sub-domains are independent, so no block waits
+// for another.  (The single-field derivative along x keeps its whole staged
+// tile and takes the end values from it.)
 #include "line_solve.cuh"
 
 namespace nopcs {
@@ -47,15 +47,16 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
     constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
     constexpr int U = 4;                               // loads in flight per thread and pass
-    // y, z: the end-row dot products are summed while staging (STREAM) and
-    // only the solve window is kept; x: the whole staged tile is kept and the
-    // solve takes the dot products from it (a warp walks one line at a time
-    // there, and a per-line warp reduction costs more than it saves)
-    constexpr bool STREAM = AXIS != 0;
+    // STREAM: the end-row dot products are summed while staging and only the
+    // solve window is kept (four blocks per SM instead of three for the flux
+    // sweeps); along x a warp walks one line and reduces its lanes' sums with
+    // shuffles.  The single-field derivative along x keeps the whole staged
+    // tile and takes the dot products in the solve (faster there).
+    constexpr bool STREAM = AXIS != 0 || MODE != MODE_FIELD;
     const int LINES = a.lines, LP = a.lines + 1, RW = STREAM ? a.rw : a.rt;
     const int KC = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
-    // row groups sharing a line while staging along y, z
-    const int RG = STREAM ? (int)blockDim.x / LINES : 0;
+    // row groups sharing a line while staging along y, z (one warp along x)
+    const int RG = STREAM ? (AXIS == 0 ? 1 : (int)blockDim.x / LINES) : 0;
     // shared memory: end-row taps (2 x max_taps), Thomas factors (2 x KC),
     // end-row partial sums [RG][2][NF][LINES], tile [NF][RW][LP]
     T *cs = reinterpret_cast<T *>(smraw);
@@ -190,11 +191,30 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                 }
             }
             if constexpr (STREAM) {
-                T *pp = part + l + (size_t)r0 * 2 * NF * LINES;  // [k][which][f][line]
+                if constexpr (AXIS == 0) {
+                    __syncwarp();
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    pp[(size_t)f * LINES] = ps[f];
-                    pp[(size_t)(NF + f) * LINES] = pe[f];
+                    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            ps[f] += __shfl_xor_sync(0xffffffffu, ps[f], o);
+                            pe[f] += __shfl_xor_sync(0xffffffffu, pe[f], o);
+                        }
+                    }
+                    if (r0 == 0) {
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            part[(size_t)f * LINES + l] = ps[f];
+                            part[(size_t)(NF + f) * LINES + l] = pe[f];
+                        }
+                    }
+                } else {
+                    T *pp = part + l + (size_t)r0 * 2 * NF * LINES;  // [k][which][f][line]
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        pp[(size_t)f * LINES] = ps[f];
+                        pp[(size_t)(NF + f) * LINES] = pe[f];
+                    }
                 }
             }
         }
@@ -299,7 +319,7 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
     a.rt = op.max_tile;
     a.rw = op.max_win;
-    const int rows = AXIS == 0 ? a.rt : a.rw;
+    const int rows = (AXIS != 0 || MODE != MODE_FIELD) ? a.rw : a.rt;
     a.lines = pick_lines(pref_lines, rows, NF, sizeof(T));
     const int kc = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
     const int Na = AXIS == 0 ? a.n[1] : a.n[0];
@@ -318,7 +338,7 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     if (threads < 128) threads = 128;
     if (threads > 1024) threads = (a.lines * NF + 31) / 32 * 32;
     if (threads > 1024) return cudaErrorInvalidConfiguration;
-    const int rg = AXIS == 0 ? 0 : threads / a.lines;
+    const int rg = (AXIS != 0 || MODE != MODE_FIELD) ? (AXIS == 0 ? 1 : threads / a.lines) : 0;
     const size_t smem = ((size_t)NF * rows * (a.lines + 1) + 2 * (size_t)op.max_taps + 2 * (size_t)kc +
                          (size_t)rg * 2 * NF * a.lines) *
                         sizeof(T);

@@ -20,7 +20,8 @@ _SRC = os.path.join(_HERE, "nopcs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OUCS3 = (0.3793894912, 0.7877868952, 0.045801298, -0.025)  # alpha, b1, b2, beta
-DERIV, FILTER = 0, 1
+DERIV, FILTER, D2 = 0, 1, 2
+LELE_D2 = (2.0 / 11.0, 12.0 / 11.0, 3.0 / 11.0)  # alpha, a, b of the sixth-order compact second derivative
 THRESH_FP64 = 1e-16
 
 
@@ -103,7 +104,7 @@ class Op:
     def __init__(self, N: int, kind: int = DERIV, sub_n: int = 0, thresh: float = THRESH_FP64,
                  coef=None):
         if coef is None:
-            coef = OUCS3 if kind == DERIV else (0.135,)
+            coef = {DERIV: OUCS3, FILTER: (0.135,), D2: LELE_D2}[kind]
         self._coef = np.ascontiguousarray(coef, dtype=np.float64)
         self.N = N
         self._p = lib().orc_op_new(N, kind, self._coef, sub_n, thresh)
@@ -148,7 +149,7 @@ def deriv3d(f, axis: int, h: float, sub_n: int, thresh: float = THRESH_FP64, den
     N = (nx, ny, nz)[axis]
     op = Op(N, kind, sub_n, thresh)
     out = np.empty_like(f)
-    scale = 1.0 / h if kind == DERIV else 1.0
+    scale = {DERIV: 1.0 / h, FILTER: 1.0, D2: 1.0 / (h * h)}[kind]
     lib().orc_apply_axis(op._p, nx, ny, nz, axis, f, out, scale, int(dense))
     return out
 

@@ -55,7 +55,7 @@
 /* 1. Line operators: [A]{g} = [B]{f} with tridiagonal A                      */
 /* ------------------------------------------------------------------------- */
 
-enum { ORC_DERIV = 0, ORC_FILTER = 1 };
+enum { ORC_DERIV = 0, ORC_FILTER = 1, ORC_D2 = 2 };
 
 typedef struct {
     int N;         /* points on the line                                      */
@@ -125,6 +125,12 @@ static void dense_solve(int N, double *A, double *Y)
  * coef for ORC_DERIV: {alpha, b1, b2, beta}  (OUCS3 eta=0: 0.3793894912,
  *   0.7877868952, 0.045801298; wall closure beta = -0.025).
  * coef for ORC_FILTER: {alpha_f}.
+ * coef for ORC_D2: {alpha, a, b}: the tridiagonal sixth-order compact second
+ *   derivative of Lele (J. Comput. Phys. 103, 1992), alpha = 2/11, a = 12/11,
+ *   b = 3/11 -- the option the paper's viscous-term remark leaves open; its
+ *   wall rows are a reading (the paper gives none): explicit one-sided
+ *   (2, -5, 4, -1) at rows 0 and N-1 and central (1, -2, 1) at rows 1 and N-2,
+ *   mirrored symmetrically.  B is dimensionless (second derivative times h^2).
  * Returns NULL if N is too small.
  */
 orc_op *orc_op_new(int N, int kind, const double *coef, int sub_n, double thresh)
@@ -164,6 +170,30 @@ orc_op *orc_op_new(int N, int kind, const double *coef, int sub_n, double thresh
         for (int j = 0; j < 5; ++j) {
             op->B[1 * (size_t)N + j] = r1[j];
             op->B[(size_t)(N - 2) * N + (N - 1 - j)] = -r1[j];
+        }
+    } else if (kind == ORC_D2) {
+        double al = coef[0], a = coef[1], b = coef[2];
+        op->nexp = 2;
+        op->alpha = al;
+        /* interior rows: alpha f''_{i-1} + f''_i + alpha f''_{i+1}
+         *   = a (f_{i+1} - 2 f_i + f_{i-1}) + (b/4) (f_{i+2} - 2 f_i + f_{i-2}) */
+        for (int i = 2; i <= N - 3; ++i) {
+            A[(size_t)i * N + i - 1] = al;
+            A[(size_t)i * N + i + 1] = al;
+            op->B[(size_t)i * N + i - 2] = 0.25 * b;
+            op->B[(size_t)i * N + i - 1] = a;
+            op->B[(size_t)i * N + i] = -2.0 * a - 0.5 * b;
+            op->B[(size_t)i * N + i + 1] = a;
+            op->B[(size_t)i * N + i + 2] = 0.25 * b;
+        }
+        double r0[4] = {2.0, -5.0, 4.0, -1.0}, r1[3] = {1.0, -2.0, 1.0};
+        for (int j = 0; j < 4; ++j) {
+            op->B[0 * (size_t)N + j] = r0[j];
+            op->B[(size_t)(N - 1) * N + (N - 1 - j)] = r0[j];
+        }
+        for (int j = 0; j < 3; ++j) {
+            op->B[1 * (size_t)N + j] = r1[j];
+            op->B[(size_t)(N - 2) * N + (N - 1 - j)] = r1[j];
         }
     } else {
         double af = coef[0];

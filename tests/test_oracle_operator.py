@@ -221,3 +221,60 @@ def test_explicit_second_order_operator():
     f = np.broadcast_to(x ** 2, (3, 4, 12)).copy()
     d = oracle.explicit2(f, 0, 0.1)
     assert np.max(np.abs(d - 2 * x)) < 1e-12
+
+
+# ---- the compact second derivative (Lele's sixth-order tridiagonal scheme) ----
+
+def test_d2_coefficients_are_consistent():
+    """The Taylor conditions of the tridiagonal second-derivative family at
+    orders 2, 4 and 6: a + b = 1 + 2 alpha, a + 4b = 12 alpha, a + 16b = 30 alpha."""
+    al, a, b = oracle.LELE_D2
+    assert abs((a + b) - (1 + 2 * al)) < 1e-15
+    assert abs((a + 4 * b) - 12 * al) < 1e-14
+    assert abs((a + 16 * b) - 30 * al) < 1e-14
+
+
+@pytest.mark.parametrize("sub_n", [0, 3, 5, 8])
+def test_d2_exact_for_cubics(sub_n):
+    N = 30
+    x = np.linspace(0.0, 1.0, N)
+    h = x[1] - x[0]
+    f = 1 + 2 * x - 3 * x ** 2 + 0.7 * x ** 3
+    g = oracle.Op(N, kind=oracle.D2, sub_n=sub_n).nopcs(f) / h ** 2
+    assert np.max(np.abs(g - (-6 + 4.2 * x))) < 1e-11
+
+
+def test_d2_modified_wavenumber_in_the_interior():
+    """Away from the walls sin(kx) gets -k_eq^2 sin(kx) with
+    k_eq^2 h^2 = [2a (1 - cos kh) + (b/2)(1 - cos 2kh)] / (1 + 2 alpha cos kh)."""
+    al, a, b = oracle.LELE_D2
+    N = 200
+    x = np.arange(N) * 1.0
+    for kh in (0.3, 1.0, 2.0, 2.9):
+        f = np.sin(kh * x + 0.4)
+        g = oracle.Op(N, kind=oracle.D2, sub_n=0).nopcs(f)
+        keq2 = (2 * a * (1 - np.cos(kh)) + 0.5 * b * (1 - np.cos(2 * kh))) / (1 + 2 * al * np.cos(kh))
+        i = slice(40, N - 40)
+        assert np.max(np.abs(g[i] + keq2 * f[i])) < 1e-12
+
+
+def test_d2_sixth_order_in_the_interior():
+    errs = []
+    for N in (41, 81):
+        x = np.linspace(0, 1, N)
+        h = x[1] - x[0]
+        f = np.sin(2 * np.pi * x + 0.3)
+        g = oracle.Op(N, kind=oracle.D2, sub_n=0).nopcs(f) / h ** 2
+        c = N // 2
+        errs.append(abs(g[c] + (2 * np.pi) ** 2 * f[c]))
+    assert 50 < errs[0] / errs[1] < 80  # 2^6 = 64
+
+
+def test_d2_subdomain_independence():
+    N = 61
+    rng = np.random.default_rng(5)
+    f = np.cumsum(rng.standard_normal(N)) * 0.1
+    ref = oracle.Op(N, kind=oracle.D2, sub_n=0).dense(f)
+    for sub_n in (3, 5, 8, 24, 0):
+        g = oracle.Op(N, kind=oracle.D2, sub_n=sub_n).nopcs(f)
+        assert np.max(np.abs(g - ref)) <= 1e-13 * np.max(np.abs(ref))

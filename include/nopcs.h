@@ -144,16 +144,21 @@ nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box);
 
 /*
  * NOHAP compact derivative of one field of box `box`'s shape along `axis`
- * (0 = x, 1 = y, 2 = z), scaled by 1/h_axis.  order 1: the OUCS3 first
- * derivative (Sec. 3).  order 2: the first-derivative operator applied twice
+ * (0 = x, 1 = y, 2 = z).  order 1: the OUCS3 first derivative (Sec. 3),
+ * scaled by 1/h.  order 2: the first-derivative operator applied twice
  * (the paper prints no compact second derivative; this reading is stated in the
- * design notes).  dtype 0: f and df are FP64 and the arithmetic is FP64 with C
+ * design notes).  order NOPCS_ORDER_D2_COMPACT (3): the sixth-order tridiagonal
+ * compact second derivative of Lele (alpha 2/11, a 12/11, b 3/11), scaled by
+ * 1/h^2, with its own NOHAP closure (end rows of its global C = A^-1 B) and the
+ * wall rows stated in the design notes; always the Thomas form.
+ * dtype 0: f and df are FP64 and the arithmetic is FP64 with C
  * rows truncated at |C| < 1e-16 (48 taps each side, Sec. 3); dtype 1: FP32 with
  * C rows truncated at |C| < 1e-8 (24 taps each side).  f and df are device
  * pointers of np elements, must not overlap; the work is enqueued on `stream`
  * and the call does not wait.  order 2 uses library-owned scratch of np
  * elements.  Errors: EINVAL, ECUDA.
  */
+enum { NOPCS_ORDER_D2_COMPACT = 3 };
 nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int dtype,
                               const void *f, void *df, void *stream);
 

@@ -33,6 +33,7 @@ struct BoxRes {
     BoxDev dev{};
     LineOpBuf dop64[3], dop32[3], fop[3];
     LineOpBuf fop32[3];  // mixed form: the filter with FP32 end-row tables
+    LineOpBuf d2op64[3], d2op32[3];  // compact second derivative (nopcs_derivative order 3)
     GemmOpBuf gop[3];  // dense blocks of the FP32 derivative (tensor-core form)
     int sub_n[3] = {0, 0, 0};     // sub-domain length in use per axis (tuned if asked)
     int lines[3] = {0, 0, 0};     // flux-sweep lines per block per axis (0: default)
@@ -166,6 +167,8 @@ void free_box(BoxRes &b)
         b.dop32[a].release();
         b.fop[a].release();
         b.fop32[a].release();
+        b.d2op64[a].release();
+        b.d2op32[a].release();
         b.gop[a].release();
         b.bop[a].release();
     }
@@ -193,6 +196,11 @@ nopcs_status build_axis_ops(nopcs_ctx *ctx, BoxRes &b, int a)
     CK(b.dop64[a].upload(), "operator upload");
     CK(b.dop32[a].upload(), "operator upload");
     CK(b.fop[a].upload(), "operator upload");
+    if (!build_line_op(d.n[a], sn, KIND_D2, 0.0, 1e-16, b.d2op64[a].host, msg) ||
+        !build_line_op(d.n[a], sn, KIND_D2, 0.0, 1e-8, b.d2op32[a].host, msg))
+        return fail(ctx, NOPCS_EINVAL, msg);
+    CK(b.d2op64[a].upload(), "operator upload");
+    CK(b.d2op32[a].upload(), "operator upload");
     if (b.mixed) {
         if (!build_line_op(d.n[a], sn, KIND_FILTER, d.filter_alpha, 1e-8, b.fop32[a].host, msg))
             return fail(ctx, NOPCS_EINVAL, msg);
@@ -759,7 +767,8 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
     nopcs_status s = check_box(ctx, box);
     if (s != NOPCS_OK) return s;
     if (axis < 0 || axis > 2) return fail(ctx, NOPCS_EINVAL, "axis must be 0, 1 or 2");
-    if (order != 1 && order != 2) return fail(ctx, NOPCS_EINVAL, "order must be 1 or 2");
+    if (order != 1 && order != 2 && order != NOPCS_ORDER_D2_COMPACT)
+        return fail(ctx, NOPCS_EINVAL, "order must be 1, 2 or NOPCS_ORDER_D2_COMPACT");
     if (dtype != 0 && dtype != 1) return fail(ctx, NOPCS_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
     if (!f || !df) return fail(ctx, NOPCS_EINVAL, "null field pointer");
     BoxRes &b = ctx->boxes[box];
@@ -769,6 +778,15 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
     if (fc < dc + bytes && dc < fc + bytes) return fail(ctx, NOPCS_EINVAL, "f and df overlap");
     cudaStream_t st = (cudaStream_t)stream;
     const double scale = b.dev.inv_h[axis];
+    if (order == NOPCS_ORDER_D2_COMPACT) {
+        const double s2 = scale * scale;
+        cudaError_t e = dtype == 0 ? launch_line_field2<double>(b.d2op64[axis].dev, axis, b.dev.n, (const double *)f,
+                                                                (double *)df, s2, st)
+                                   : launch_line_field2<float>(b.d2op32[axis].dev, axis, b.dev.n, (const float *)f,
+                                                               (float *)df, s2, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
+        return NOPCS_OK;
+    }
     const LineOpDev &op = dtype == 0 ? b.dop64[axis].dev : b.dop32[axis].dev;
     const void *src = f;
     if (order == 2) {

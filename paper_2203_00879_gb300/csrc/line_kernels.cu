@@ -44,15 +44,16 @@ template <typename T, int MODE, int AXIS>
 __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
-    constexpr int NIN = MODE == MODE_FIELD ? 1 : (MODE == MODE_FLUX ? 6 : 5);
+    constexpr bool SINGLE = MODE == MODE_FIELD || MODE == MODE_FIELD2;  // one field in, one out
+    constexpr int NF = SINGLE ? 1 : 5;
+    constexpr int NIN = SINGLE ? 1 : (MODE == MODE_FLUX ? 6 : 5);
     constexpr int U = 4;                               // loads in flight per thread and pass
     // STREAM: the end-row dot products are summed while staging and only the
     // solve window is kept (four blocks per SM instead of three for the flux
     // sweeps); along x a warp walks one line and reduces its lanes' sums with
     // shuffles.  The single-field derivative along x keeps the whole staged
     // tile and takes the dot products in the solve (faster there).
-    constexpr bool STREAM = AXIS != 0 || MODE != MODE_FIELD;
+    constexpr bool STREAM = AXIS != 0 || !SINGLE;
     const int LINES = a.lines, LP = a.lines + 1, RW = STREAM ? a.rw : a.rt;
     const int KC = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
     // row groups sharing a line while staging along y, z (one warp along x)
@@ -148,7 +149,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                     if (rr >= nrows) continue;
                     const int g = tlo + rr;
                     T val[NF];
-                    if constexpr (MODE == MODE_FIELD) {
+                    if constexpr (SINGLE) {
                         val[0] = v[u][0];
                     } else if constexpr (MODE == MODE_FLUX) {
                         const int gk = gsel == 0 ? g : gl;
@@ -280,7 +281,7 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                     if (rr >= nown) continue;
                     const T *src = srcs + (size_t)rr * LP;
                     const int o = dstg + rr * srow;
-                    if constexpr (MODE == MODE_FIELD) {
+                    if constexpr (SINGLE) {
                         a.out[0][o] = src[0] * a.scale;
                     } else if constexpr (MODE == MODE_FLUX) {
 #pragma unroll
@@ -316,10 +317,11 @@ int pick_lines(int pref, int rw, int nf, size_t esz)
 template <typename T, int MODE, int AXIS>
 cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cudaStream_t st)
 {
-    constexpr int NF = MODE == MODE_FIELD ? 1 : 5;
+    constexpr bool SINGLE = MODE == MODE_FIELD || MODE == MODE_FIELD2;
+    constexpr int NF = SINGLE ? 1 : 5;
     a.rt = op.max_tile;
     a.rw = op.max_win;
-    const int rows = (AXIS != 0 || MODE != MODE_FIELD) ? a.rw : a.rt;
+    const int rows = (AXIS != 0 || !SINGLE) ? a.rw : a.rt;
     a.lines = pick_lines(pref_lines, rows, NF, sizeof(T));
     const int kc = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
     const int Na = AXIS == 0 ? a.n[1] : a.n[0];
@@ -338,7 +340,7 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     if (threads < 128) threads = 128;
     if (threads > 1024) threads = (a.lines * NF + 31) / 32 * 32;
     if (threads > 1024) return cudaErrorInvalidConfiguration;
-    const int rg = (AXIS != 0 || MODE != MODE_FIELD) ? (AXIS == 0 ? 1 : threads / a.lines) : 0;
+    const int rg = (AXIS != 0 || !SINGLE) ? (AXIS == 0 ? 1 : threads / a.lines) : 0;
     const size_t smem = ((size_t)NF * rows * (a.lines + 1) + 2 * (size_t)op.max_taps + 2 * (size_t)kc +
                          (size_t)rg * 2 * NF * a.lines) *
                         sizeof(T);
@@ -377,7 +379,10 @@ cudaError_t init_line_kernels()
         allow_smem<double, MODE_FLUX, 0>(),  allow_smem<double, MODE_FLUX, 1>(),  allow_smem<double, MODE_FLUX, 2>(),
         allow_smem<double, MODE_FILTER, 0>(), allow_smem<double, MODE_FILTER, 1>(),
         allow_smem<double, MODE_FILTER, 2>(),  allow_smem<float, MODE_FILTER, 0>(),
-        allow_smem<float, MODE_FILTER, 1>(),   allow_smem<float, MODE_FILTER, 2>()};
+        allow_smem<float, MODE_FILTER, 1>(),   allow_smem<float, MODE_FILTER, 2>(),
+        allow_smem<float, MODE_FIELD2, 0>(),   allow_smem<float, MODE_FIELD2, 1>(),
+        allow_smem<float, MODE_FIELD2, 2>(),   allow_smem<double, MODE_FIELD2, 0>(),
+        allow_smem<double, MODE_FIELD2, 1>(),  allow_smem<double, MODE_FIELD2, 2>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -449,6 +454,22 @@ cudaError_t launch_line_filter32(const LineOpDev &op, int axis, const BoxDev &bx
     return launch_any<float, MODE_FILTER>(op, axis, a, 32, st);
 }
 
+template <typename T>
+cudaError_t launch_line_field2(const LineOpDev &op, int axis, const int n[3], const T *f, T *out, double scale,
+                               cudaStream_t st)
+{
+    LineArgs<T> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = n[d];
+    a.in[0] = f;
+    a.out[0] = out;
+    a.scale = (T)scale;
+    return launch_any<T, MODE_FIELD2>(op, axis, a, sizeof(T) == 4 ? 64 : 32, st);
+}
+
+template cudaError_t launch_line_field2<float>(const LineOpDev &, int, const int *, const float *, float *, double,
+                                               cudaStream_t);
+template cudaError_t launch_line_field2<double>(const LineOpDev &, int, const int *, const double *, double *,
+                                                double, cudaStream_t);
 template cudaError_t launch_line_field<float>(const LineOpDev &, int, const int *, const float *, float *,
                                               double, cudaStream_t);
 template cudaError_t launch_line_field<double>(const LineOpDev &, int, const int *, const double *,

@@ -112,6 +112,8 @@ __device__ __forceinline__ void nohap_solve_column(const LineOpDev &op, T *col, 
             T rhs;
             if constexpr (MODE == MODE_FILTER)
                 rhs = r0 * win[3] + r1 * (win[4] + win[2]) + r2 * (win[5] + win[1]) + r3 * (win[6] + win[0]);
+            else if constexpr (MODE == MODE_FIELD2)
+                rhs = r0 * win[2] + r1 * (win[3] + win[1]) + r2 * (win[4] + win[0]);
             else
                 rhs = r0 * (win[3] - win[1]) + r1 * (win[4] - win[0]);
             const T dp = (rhs - adj - al * dprev) * iv;

@@ -12,8 +12,11 @@
 
 namespace nopcs {
 
-enum LineKind { KIND_DERIV = 0, KIND_FILTER = 1 };
-enum LineMode { MODE_FIELD = 0, MODE_FLUX = 1, MODE_FILTER = 2 };
+// KIND_D2: the sixth-order compact second derivative (a symmetric right-hand
+// side like the filter's, explicit wall rows like the derivative's)
+enum LineKind { KIND_DERIV = 0, KIND_FILTER = 1, KIND_D2 = 2 };
+// MODE_FIELD2: one field through a KIND_D2 operator
+enum LineMode { MODE_FIELD = 0, MODE_FLUX = 1, MODE_FILTER = 2, MODE_FIELD2 = 3 };
 
 // Per-sub-domain record of a line operator (ints, device array of nsub * SUB_REC).
 //   [0] s, [1] e            sub-domain rows (inclusive)
@@ -163,6 +166,10 @@ cudaError_t init_line_kernels();
 template <typename T>
 cudaError_t launch_line_field(const LineOpDev &op, int axis, const int n[3], const T *f, T *out,
                               double scale, cudaStream_t st);
+// FIELD2: out = scale * L2 f with a KIND_D2 operator (scale = 1 / h^2).
+template <typename T>
+cudaError_t launch_line_field2(const LineOpDev &op, int axis, const int n[3], const T *f, T *out, double scale,
+                               cudaStream_t st);
 // FLUX: R (= or -=) L(flux_axis(W)) / h.  first != 0 stores, else subtracts.
 // lines: lines per block (tile width; 0 = default for the precision).
 template <typename T>

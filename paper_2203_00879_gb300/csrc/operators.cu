@@ -184,6 +184,27 @@ bool build_line_op(int N, int sub_n, int kind, double alpha_f, double thresh, Li
             op.ex[1][j] = r1[j];
         }
         op.ex_sign = -1.0;
+    } else if (kind == KIND_D2) {
+        // Lele's sixth-order tridiagonal second derivative: alpha = 2/11,
+        // a = 12/11, b = 3/11, right-hand side
+        // a (f[i+1] - 2 f[i] + f[i-1]) + (b/4)(f[i+2] - 2 f[i] + f[i-2]) (times
+        // h^2); wall rows (a reading: the paper gives none): one-sided
+        // (2, -5, 4, -1) at rows 0 and N-1, central (1, -2, 1) at rows 1 and N-2
+        op.nexp = 2;
+        op.alpha = 2.0 / 11.0;
+        const double a = 12.0 / 11.0, b = 3.0 / 11.0;
+        op.rb[0] = -2.0 * a - 0.5 * b;
+        op.rb[1] = a;
+        op.rb[2] = 0.25 * b;
+        op.rb[3] = 0.0;
+        w = 2;
+        const double r0[5] = {2.0, -5.0, 4.0, -1.0, 0.0};
+        const double r1[5] = {1.0, -2.0, 1.0, 0.0, 0.0};
+        for (int j = 0; j < 5; ++j) {
+            op.ex[0][j] = r0[j];
+            op.ex[1][j] = r1[j];
+        }
+        op.ex_sign = 1.0;
     } else {
         op.nexp = 3;
         op.alpha = alpha_f;
@@ -356,6 +377,8 @@ void apply_line_host(const LineOpHost &op, const double *f, double *g)
                 double rhs;
                 if (op.kind == KIND_DERIV)
                     rhs = op.rb[0] * (f[i + 1] - f[i - 1]) + op.rb[1] * (f[i + 2] - f[i - 2]);
+                else if (op.kind == KIND_D2)
+                    rhs = op.rb[0] * f[i] + op.rb[1] * (f[i + 1] + f[i - 1]) + op.rb[2] * (f[i + 2] + f[i - 2]);
                 else
                     rhs = op.rb[0] * f[i] + op.rb[1] * (f[i + 1] + f[i - 1]) + op.rb[2] * (f[i + 2] + f[i - 2]) +
                           op.rb[3] * (f[i + 3] + f[i - 3]);
@@ -590,7 +613,7 @@ using namespace nopcs;
 extern "C" nopcs_status nopcs_band_apply(int N, int kind, double alpha_f, double thresh, const double *f, double *g,
                                          int *half_width, int *interior_lo, int *interior_hi)
 {
-    if (kind != KIND_DERIV && kind != KIND_FILTER) return NOPCS_EINVAL;
+    if (kind != KIND_DERIV && kind != KIND_FILTER && kind != KIND_D2) return NOPCS_EINVAL;
     if (!f || !g) return NOPCS_EINVAL;
     BandHost bh;
     std::string msg;
@@ -606,7 +629,7 @@ extern "C" nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double a
                                             int *nsub, int *starts, int *end_j0, int *end_len,
                                             double *coef, int max_coef)
 {
-    if (kind != KIND_DERIV && kind != KIND_FILTER) return NOPCS_EINVAL;
+    if (kind != KIND_DERIV && kind != KIND_FILTER && kind != KIND_D2) return NOPCS_EINVAL;
     LineOpHost op;
     std::string msg;
     if (!build_line_op(N, sub_n, kind, alpha_f, thresh, op, msg)) return NOPCS_EINVAL;
@@ -633,7 +656,7 @@ extern "C" nopcs_status nopcs_operator_rows(int N, int sub_n, int kind, double a
 extern "C" nopcs_status nopcs_operator_apply(int N, int sub_n, int kind, double alpha_f, double thresh,
                                              const double *f, double *g)
 {
-    if (kind != KIND_DERIV && kind != KIND_FILTER) return NOPCS_EINVAL;
+    if (kind != KIND_DERIV && kind != KIND_FILTER && kind != KIND_D2) return NOPCS_EINVAL;
     if (!f || !g) return NOPCS_EINVAL;
     LineOpHost op;
     std::string msg;

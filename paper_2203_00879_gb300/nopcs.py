@@ -175,6 +175,7 @@ def nopcs_box_info(ctx, box: int) -> dict:
 
 
 NOPCS_PLANE_DP, NOPCS_PLANE_VORTICITY_TERMS = 0, 1
+NOPCS_ORDER_D2_COMPACT = 3
 
 
 def nopcs_plane_fields(ctx, box: int, axis: int, index: int, what: int, out_ptr: int) -> None:

@@ -67,7 +67,7 @@ def test_kernel_names(N):
 
 
 @pytest.mark.parametrize("Nn,sub_n", [(5, 3), (7, 3), (48, 24), (50, 24), (101, 24), (257, 64), (129, 0)])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_operator_tables_match_oracle(N, Nn, sub_n, kind):
     """The library's end rows (C = A^-1 B via transposed tridiagonal solves)
     equal the oracle's dense C rows, and everything dropped is below 1e-16."""
@@ -97,7 +97,7 @@ def test_fp32_tables_have_24_taps_each_side(N):
 
 
 @pytest.mark.parametrize("Nn,sub_n", [(5, 3), (9, 4), (48, 24), (50, 24), (101, 24), (257, 64), (129, 0)])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_host_line_algorithm_matches_oracle(N, Nn, sub_n, kind):
     """The library's own FP64 line algorithm (end rows, tabulated Thomas
     factors) equals the oracle's NOHAP evaluation."""

@@ -115,7 +115,7 @@ def test_derivative_rejects_bad_arguments():
     ctx, p = _ctx(N, (8, 8, 8), (0, 0, 0))
     try:
         f = torch.zeros(1024, dtype=torch.float64, device="cuda")
-        for args in ((0, 3, 1, 0), (0, 0, 3, 0), (0, 0, 1, 2), (1, 0, 1, 0)):
+        for args in ((0, 3, 1, 0), (0, 0, 4, 0), (0, 0, 0, 0), (0, 0, 1, 2), (1, 0, 1, 0)):
             box, axis, order, dt = args
             with pytest.raises(N.NopcsError):
                 N.nopcs_derivative(ctx, box, axis, order, dt, f.data_ptr(), f.data_ptr() + 4096, 0)

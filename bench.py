@@ -154,6 +154,11 @@ def run_cpu_oracle(n, steps, warmup=0):
     return pts / dt, dt, oracle.num_threads()
 
 
+def workload_name(n, sub_n):
+    return ("two-temperature Rayleigh-Taylor box %d^3, mixed precision (FP32 fluxes and NOHAP derivatives, "
+            "FP64 state and RK4), sub-domains of %d, filter every 50 steps" % (n, sub_n))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -166,7 +171,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "two-temperature RTI box %d^3 (oracle sample of the 1024^3 workload)" % n},
+            "config": {"workload": workload_name(args.n, args.sub_n), "grid": [args.n] * 3, "sub_n": args.sub_n,
+                       "precision": "fp64 (the oracle)", "sample_grid": [n] * 3,
+                       "parallelism": "rank 0 only (host cores)"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -463,9 +470,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": "two-temperature Rayleigh-Taylor box %d^3, mixed precision (FP32 fluxes and "
-                                   "NOHAP derivatives, FP64 state and RK4), sub-domains of %d, filter every 50 "
-                                   "steps" % (n, args.sub_n),
+            "config": {"workload": workload_name(n, args.sub_n),
                        "grid": [n, n, n], "sub_n": args.sub_n, "precision": "mixed", "form": "thomas",
                        "sweep_tile_lines": tile_lines,
                        "l2": "inputs larger than L2 (FP64 state %.1f GB)" % (40 * npts / 1e9),

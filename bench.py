@@ -379,7 +379,7 @@ def main():
     ms_max = rank_max(ms)
     value = job_rate(npts, 4, K, world, ms_max)
     launches_per_kind = {"prep": 1, "sweep_x": 1, "sweep_y": 1, "sweep_z": 1, "visc_rk_update": 1,
-                         "wall_bc": 2, "filter": 4, "diagnostics": 2}
+                         "wall_bc": 3, "filter": 4, "diagnostics": 2}
     gpu_launches = int(sum(v[1] * launches_per_kind.get(k, 1) for k, v in prof.items()))
 
     # dominant kernel against the HBM roofline

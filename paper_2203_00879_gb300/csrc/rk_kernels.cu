@@ -247,15 +247,18 @@ __global__ void wall_face_kernel(const BoxDev bx, double *Q, float *Dn, float *W
     }
 }
 
-// edges (two wall coordinates), then corners; one block
-__global__ void wall_edge_corner_kernel(const BoxDev bx, double *Q, float *Dn, float *Wf, float *Ww)
+// edges (two wall coordinates): every edge node reads only face and interior
+// nodes, so the edges run in parallel; the corners, which read edge nodes,
+// follow in their own launch
+__global__ void wall_edge_kernel(const BoxDev bx, double *Q, float *Dn, float *Wf, float *Ww)
 {
     const int n[3] = {bx.n[0], bx.n[1], bx.n[2]};
     // edge along axis a: the other two axes at 0 or n-1 (4 combinations)
     long long cnt[3];
     for (int a = 0; a < 3; ++a) cnt[a] = 4LL * (n[a] - 2);
     const long long tot = cnt[0] + cnt[1] + cnt[2];
-    for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
         long long q = t;
         int a = 0;
         while (q >= cnt[a]) {
@@ -274,10 +277,13 @@ __global__ void wall_edge_corner_kernel(const BoxDev bx, double *Q, float *Dn, f
         else
             set_wall_node_w(bx, Ww, c);
     }
-    __syncthreads();
+}
+
+__global__ void wall_corner_kernel(const BoxDev bx, double *Q, float *Dn, float *Wf, float *Ww)
+{
     if (threadIdx.x < 8) {
         int c[3];
-        for (int d = 0; d < 3; ++d) c[d] = (threadIdx.x >> d) & 1 ? n[d] - 1 : 0;
+        for (int d = 0; d < 3; ++d) c[d] = (threadIdx.x >> d) & 1 ? bx.n[d] - 1 : 0;
         if (Q)
             set_wall_node(bx, Q, c, Dn, Wf);
         else
@@ -445,7 +451,11 @@ cudaError_t launch_wall_bc(const BoxDev &bx, double *Q, float *Dn, float *Wf, fl
     wall_face_kernel<<<grid_for(faces, 256), 256, 0, st>>>(bx, Q, Dn, Wf, Ww);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    wall_edge_corner_kernel<<<1, 512, 0, st>>>(bx, Q, Dn, Wf, Ww);
+    const long long edges = 4LL * ((bx.n[0] - 2) + (bx.n[1] - 2) + (bx.n[2] - 2));
+    wall_edge_kernel<<<grid_for(edges, 256), 256, 0, st>>>(bx, Q, Dn, Wf, Ww);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wall_corner_kernel<<<1, 32, 0, st>>>(bx, Q, Dn, Wf, Ww);
     return cudaGetLastError();
 }
 

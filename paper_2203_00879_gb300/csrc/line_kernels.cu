@@ -264,17 +264,6 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
             const T *srcs = sm + (size_t)(s - org) * LP + ll;
             const int gl = gsel == 1 ? a0 + ll : cc;
             for (int r = r0; r < nown; r += U * rstep) {
-                T old[U][5];
-                if (MODE == MODE_FLUX && !a.first) {
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int rr = r + u * rstep;
-                        if (rr < nown) {
-#pragma unroll
-                            for (int f = 0; f < 5; ++f) old[u][f] = a.out[f][dstg + rr * srow];
-                        }
-                    }
-                }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int rr = r + u * rstep;
@@ -287,7 +276,15 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 #pragma unroll
                         for (int f = 0; f < 5; ++f) {
                             const T v = -src[f * fs] * a.scale;
-                            a.out[f][o] = a.first ? v : old[u][f] + v;
+                            // later sweeps add through a reduction performed
+                            // in L2 (the old value never travels to the SM,
+                            // so the store phase waits on no load); every
+                            // element takes exactly one addition per sweep,
+                            // the same rounding as load + add + store
+                            if (a.first)
+                                a.out[f][o] = v;
+                            else
+                                atomicAdd(&a.out[f][o], v);
                         }
                     } else {
                         const int gk = gsel == 0 ? s + rr : gl;

@@ -37,7 +37,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 def box_params(n=(48, 48, 48), *, sub_n=(24, 24, 24), length=None, gravity_axis=2,
                T_upper=1.0, T_lower=500.0 / 300.0, dt=DT_ND, filter_every=50,
                filter_alpha=0.135, base_subtract=0, seed=1, perturb_amp=1e-6,
-               Re=RE, M=MACH, Pr=PR, gamma=GAMMA, mub_scale=1.0, g=1.0):
+               Re=RE, M=MACH, Pr=PR, gamma=GAMMA, mub_scale=1.0, g=1.0, visc_compact=0):
     """One box of the two-temperature Rayleigh-Taylor setup (plain dict).
 
     Nodes sit on the walls with a uniform spacing h = 1/(n_x - 1) unless
@@ -53,7 +53,7 @@ def box_params(n=(48, 48, 48), *, sub_n=(24, 24, 24), length=None, gravity_axis=
                 mu_s_si=MU_S_SI, Ts_kelvin=TS_KELVIN, T_upper=float(T_upper),
                 T_lower=float(T_lower), g=float(g), dt=float(dt), filter_every=int(filter_every),
                 filter_alpha=float(filter_alpha), base_subtract=int(base_subtract),
-                seed=int(seed), perturb_amp=float(perturb_amp))
+                seed=int(seed), perturb_amp=float(perturb_amp), visc_compact=int(visc_compact))
 
 
 def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:

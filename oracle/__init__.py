@@ -42,7 +42,7 @@ class _Box(C.Structure):
                 ("mu_s_si", C.c_double), ("Ts_kelvin", C.c_double), ("T_upper", C.c_double),
                 ("T_lower", C.c_double), ("g", C.c_double), ("dt", C.c_double),
                 ("filter_every", C.c_int), ("filter_alpha", C.c_double), ("base_subtract", C.c_int),
-                ("seed", C.c_ulonglong), ("perturb_amp", C.c_double)]
+                ("seed", C.c_ulonglong), ("perturb_amp", C.c_double), ("visc_compact", C.c_int)]
 
 
 _lib = None

@@ -15,8 +15,10 @@
  *     to the second-last point of every sub-domain;
  *   - the nondimensional compressible Navier-Stokes right-hand side (Sec. 2,
  *     Eqs. ge1-ge8a, ge12-ge20, reg, bv1-bv3), second-order explicit viscous
- *     terms, classical four-stage RK4 and the implicit filter with coefficient
- *     0.135 applied every 50 steps (Sec. 4, first paragraph);
+ *     terms (or, as an option beyond the paper, viscous gradients and
+ *     divergence by the same NOHAP/OUCS3 operator), classical four-stage RK4
+ *     and the implicit filter with coefficient 0.135 applied every 50 steps
+ *     (Sec. 4, first paragraph);
  *   - the hydrostatic two-temperature initial state (Sec. 2), the
  *     diagnostics (disturbance pressure, Sec. 4) and the plane diagnostics of
  *     Sec. 4 (disturbance pressure planes and lines, the three right-hand-side
@@ -424,6 +426,9 @@ typedef struct {
     int base_subtract; /* differentiate p - p_h and use rho - rho_h in source */
     unsigned long long seed;
     double perturb_amp;
+    int visc_compact;  /* 1: viscous gradients and divergence by the compact  */
+                       /* operator of the convective terms instead of the     */
+                       /* second-order explicit differences                   */
 } orc_box;
 
 typedef struct {
@@ -561,6 +566,19 @@ static double bulk_ratio(const orc_box *bx, double T)
  * same explicit derivative of the nodal viscous fluxes.  The normal heat flux
  * is zero on adiabatic walls.
  */
+/* First derivative along axis d inside the viscous terms: the second-order
+ * explicit differences the paper uses (Sec. 4), or, with visc_compact, the
+ * NOHAP/OUCS3 operator of the convective terms (Sec. 3) -- an option beyond the
+ * paper's own choice, with the same wall closure rows and sub-domains. */
+static void visc_deriv(const orc_solver *s, int d, const double *f, double *out)
+{
+    const orc_box *bx = &s->bx;
+    if (bx->visc_compact)
+        orc_apply_axis(s->dop[d], bx->n[0], bx->n[1], bx->n[2], d, f, out, 1.0 / s->h[d], 0);
+    else
+        orc_d2_axis(bx->n[0], bx->n[1], bx->n[2], d, s->h[d], f, out);
+}
+
 void orc_rhs(orc_solver *s, const double *Q, double *R)
 {
     const orc_box *bx = &s->bx;
@@ -616,7 +634,7 @@ void orc_rhs(orc_solver *s, const double *Q, double *R)
     /* nodal gradients of u, v, w, T */
     const double *prim[4] = {u, v, wv, T};
     for (int q = 0; q < 4; ++q)
-        for (int d = 0; d < 3; ++d) orc_d2_axis(nx, ny, nz, d, s->h[d], prim[q], grad + (3 * q + d) * np);
+        for (int d = 0; d < 3; ++d) visc_deriv(s, d, prim[q], grad + (3 * q + d) * np);
 
     /* viscous fluxes Ev (d=0), Fv (d=1), Gv (d=2) and their divergence */
     double kq = 1.0 / ((gam - 1.0) * bx->Pr * bx->Re * bx->M * bx->M);
@@ -644,7 +662,7 @@ void orc_rhs(orc_solver *s, const double *Q, double *R)
             vflux[3 * np + p] = u[p] * tau[0] + v[p] * tau[1] + wv[p] * tau[2] - qd;
         }
         for (int c = 0; c < 4; ++c) {
-            orc_d2_axis(nx, ny, nz, d, s->h[d], vflux + c * np, dv);
+            visc_deriv(s, d, vflux + c * np, dv);
             for (long long p = 0; p < np; ++p) R[(1 + c) * np + p] += dv[p];
         }
     }

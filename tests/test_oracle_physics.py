@@ -126,7 +126,10 @@ def _manufactured(params):
     return fQ, fR
 
 
-def _mms_errors(params, Ns):
+def _mms_errors(params, Ns, region="inner"):
+    """Max-norm error of the discrete RHS per conserved variable, relative to
+    the symbolic RHS, over the nodes two or more away from every wall
+    ("inner") or over the middle half of the box along every axis ("mid")."""
     fQ, fR = _manufactured(params)
     errs = []
     for N in Ns:
@@ -139,7 +142,11 @@ def _mms_errors(params, Ns):
         Q = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fQ]).astype(np.float64)
         Rex = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fR])
         R = s.rhs(Q)
-        inner = np.s_[:, 2:-2, 2:-2, 2:-2]
+        if region == "mid":
+            a, b = N // 4, N - N // 4
+            inner = np.s_[:, a:b, a:b, a:b]
+        else:
+            inner = np.s_[:, 2:-2, 2:-2, 2:-2]
         e = np.abs(R - Rex)[inner].reshape(5, -1).max(axis=1) / np.abs(Rex[inner]).reshape(5, -1).max(axis=1)
         errs.append(e)
     return np.array(errs)
@@ -175,6 +182,73 @@ def test_manufactured_rhs_detects_planted_bulk_viscosity_error():
     e = np.abs(R - Rex)[inner].max() / np.abs(Rex[inner]).max()
     good = _mms_errors(params, (33,))[0][1]
     assert e > 10 * good
+
+
+def test_compact_viscous_terms_converge_and_beat_explicit():
+    """With viscous gradients and divergence by the NOHAP/OUCS3 operator the
+    discrete RHS converges to the symbolic one at least at second order and,
+    away from the walls, lies far closer to it than with the paper's
+    second-order explicit viscous terms (the operator's error constant is
+    about 1/50 of central differencing's).  Near a wall the compact divergence
+    spreads the jump that the adiabatic condition (zero normal heat flux on the
+    wall node) makes in this non-adiabatic symbolic field, so the comparison is
+    over the middle half of the box."""
+    base = S.box_params((5, 5, 5), Re=10.0, M=0.5, mub_scale=1e-3, perturb_amp=0.0, T_lower=1.0)
+    e_exp = _mms_errors(dict(base, visc_compact=0), (65,), "mid")[0]
+    e_cmp = _mms_errors(dict(base, visc_compact=1), (33, 65), "mid")
+    assert np.all(e_cmp[-1][1:] < e_exp[1:] / 10), (e_cmp, e_exp)
+    rates = np.log2(e_cmp[0] / e_cmp[1])
+    assert np.all(rates[1:] > 1.8), (e_cmp, rates)
+    # the continuity equation has no viscous term: both forms agree there
+    assert abs(e_cmp[-1][0] - e_exp[0]) <= 1e-12 * e_exp[0]
+
+
+def test_compact_viscous_detects_planted_bulk_viscosity_error():
+    params = S.box_params((5, 5, 5), Re=10.0, M=0.5, mub_scale=1e-3, perturb_amp=0.0, T_lower=1.0,
+                          visc_compact=1)
+    fQ, fR = _manufactured(params)
+    N = 33
+    p = dict(params, mub_scale=0.0, n=(N, N, N), len=(1.0, 1.0, 1.0), sub_n=(0, 0, 0))
+    zz, yy, xx = np.meshgrid(*(np.linspace(0, 1, N),) * 3, indexing="ij")
+    Q = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fQ]).astype(np.float64)
+    Rex = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in fR])
+    R = oracle.Solver(p).rhs(Q)
+    mid = np.s_[1, N // 4:N - N // 4, N // 4:N - N // 4, N // 4:N - N // 4]
+    e = np.abs(R - Rex)[mid].max() / np.abs(Rex[mid]).max()
+    good = _mms_errors(params, (N,), "mid")[0][1]
+    assert e > 10 * good
+
+
+@pytest.mark.parametrize("visc_compact", [0, 1])
+def test_linear_velocity_viscous_term_is_the_dissipation(visc_compact):
+    """Uniform density and temperature with a velocity linear in x, y, z:
+    every viscous flux derivative is of a constant or a linear function, which
+    both viscous operators (and every wall closure row) differentiate exactly.
+    The viscous part of the RHS is then zero in the momentum equations and, in
+    the energy equation, the dissipation function
+    Phi = mu/Re (sum_ij (A_ij + A_ji) A_ij - 2/3 (tr A)^2) of the velocity
+    gradient A (mu(T_s) = 1, no bulk viscosity), at every node."""
+    rng = np.random.default_rng(5)
+    A = rng.uniform(-1.0, 1.0, (3, 3))
+    c = rng.uniform(-0.5, 0.5, 3)
+    N = (9, 11, 13)
+    Re = 0.5
+    p = S.box_params(N, Re=Re, M=0.5, mub_scale=0.0, perturb_amp=0.0, T_lower=1.0, g=0.0,
+                     sub_n=(4, 5, 0), visc_compact=visc_compact)
+    h = p["len"][0] / (N[0] - 1)
+    zz, yy, xx = np.meshgrid(*(np.arange(n) * h for n in N[::-1]), indexing="ij")
+    X = (xx, yy, zz)
+    vel = [c[i] + sum(A[i, j] * X[j] for j in range(3)) for i in range(3)]
+    pr = 1.0 / (p["gamma"] * p["M"] ** 2)  # rho = T = 1
+    Q = np.stack([np.ones_like(xx), vel[0], vel[1], vel[2],
+                  pr / (p["gamma"] - 1) + 0.5 * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)])
+    R1 = oracle.Solver(p).rhs(Q)
+    R0 = oracle.Solver(dict(p, Re=1e30)).rhs(Q)
+    Rv = R1 - R0
+    phi = (np.sum((A + A.T) * A) - 2.0 / 3.0 * np.trace(A) ** 2) / Re
+    scale = np.abs(A).max() ** 2 / Re + np.abs(R0).max() * 1e-3
+    assert np.abs(Rv[1:4]).max() < 1e-10 * scale
+    assert np.abs(Rv[4] - phi).max() < 1e-10 * scale
 
 
 def test_manufactured_rhs_paper_parameters():

@@ -98,6 +98,13 @@ typedef struct {
                            /* Forced to 1 under NOPCS_MIXED.                         */
     unsigned long long seed; /* seed of the initial velocity perturbation           */
     double perturb_amp;    /* amplitude of the uniform velocity perturbation        */
+    int visc_compact;      /* 0: the paper's second-order explicit viscous terms    */
+                           /* (Sec. 4).  1: the gradients of u, v, w, T and the     */
+                           /* divergence of the viscous fluxes by the NOHAP/OUCS3   */
+                           /* operator of the convective terms, with the same wall  */
+                           /* rows and sub-domains -- an option beyond the paper;   */
+                           /* it holds 12 more fields of scratch (FP32 under        */
+                           /* NOPCS_MIXED, FP64 under NOPCS_FP64) per box           */
 } nopcs_box_desc;
 
 typedef struct {
@@ -254,7 +261,7 @@ nopcs_status nopcs_synchronize(nopcs_ctx *ctx);
  * (arrays of NOPCS_NUM_KERNELS entries).  nopcs_kernel_name gives the kind's
  * name (static string; NULL for an out-of-range id).
  */
-#define NOPCS_NUM_KERNELS 8
+#define NOPCS_NUM_KERNELS 12
 nopcs_status nopcs_set_profiling(nopcs_ctx *ctx, int on);
 nopcs_status nopcs_profile_read(nopcs_ctx *ctx, double *ms, long long *launches, int reset);
 const char *nopcs_kernel_name(int kind);

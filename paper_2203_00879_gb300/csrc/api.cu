@@ -16,9 +16,11 @@ using namespace nopcs;
 
 namespace {
 
-const char *const KERNEL_NAMES[NOPCS_NUM_KERNELS] = {"prep",         "sweep_x", "sweep_y", "sweep_z",
-                                                     "visc_rk_update", "wall_bc", "filter",  "diagnostics"};
-enum { K_PREP = 0, K_SX, K_SY, K_SZ, K_VISC, K_BC, K_FILTER, K_DIAG };
+const char *const KERNEL_NAMES[NOPCS_NUM_KERNELS] = {
+    "prep",   "sweep_x",     "sweep_y",   "sweep_z",   "visc_rk_update", "wall_bc",
+    "filter", "diagnostics", "visc_grad", "visc_flux", "visc_div",       "source_rk_update"};
+// K_VGRAD, K_VFLUX, K_VDIV, K_SRC: the compact viscous terms (visc_compact)
+enum { K_PREP = 0, K_SX, K_SY, K_SZ, K_VISC, K_BC, K_FILTER, K_DIAG, K_VGRAD, K_VFLUX, K_VDIV, K_SRC };
 
 thread_local std::string g_init_error;
 
@@ -28,6 +30,8 @@ thread_local std::string g_init_error;
 //     W0, W1 (12 fields); R = slab of R, K, Dn (15 FP32 fields).  Between
 //     steps W0 and Dn hold the primitives and the base deviation of Qn, and
 //     the filter borrows both slabs as FP64 temporaries.
+//   Compact viscous terms (visc_compact): Gv, 12 fields of the stage's
+//     precision holding the gradients of u, v, w, T, then the viscous fluxes.
 struct BoxRes {
     nopcs_box_desc d{};
     BoxDev dev{};
@@ -43,6 +47,7 @@ struct BoxRes {
     bool mixed = false;
     double *Q = nullptr;
     void *W = nullptr, *R = nullptr;
+    void *Gv = nullptr;
     void *base = nullptr;
     double *partial = nullptr, *diag_out = nullptr;
     void *scratch = nullptr;  // order-2 derivative intermediate (lazy)
@@ -138,6 +143,10 @@ bool valid_box(const nopcs_box_desc &d, std::string &m)
         m = "filter_every must be >= 0 and |filter_alpha| < 0.5";
         return false;
     }
+    if (d.visc_compact != 0 && d.visc_compact != 1) {
+        m = "visc_compact must be 0 or 1";
+        return false;
+    }
     return true;
 }
 
@@ -175,6 +184,7 @@ void free_box(BoxRes &b)
     if (b.Q) cudaFree(b.Q);
     if (b.W) cudaFree(b.W);
     if (b.R) cudaFree(b.R);
+    if (b.Gv) cudaFree(b.Gv);
     if (b.base) cudaFree(b.base);
     if (b.partial) cudaFree(b.partial);
     if (b.scratch) cudaFree(b.scratch);
@@ -450,6 +460,14 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
         b.R = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "right-hand-side buffer");
     }
+    if (d.visc_compact) {
+        e = cudaMalloc(&b.Gv, 12 * np * esize(ctx));
+        if (e != cudaSuccess) {
+            b.Gv = nullptr;
+            return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA,
+                        "compact viscous-term buffer");
+        }
+    }
     b.nblk_diag = diag_blocks(x.np);
     CK(cudaMalloc(&b.partial, ((size_t)b.nblk_diag * 10 + 16) * sizeof(double)), "diagnostics scratch");
     b.diag_out = b.partial + (size_t)b.nblk_diag * 10;
@@ -516,6 +534,50 @@ cudaError_t enqueue_rhs_sweeps(nopcs_ctx *ctx, BoxRes &b, const T *W, T *R, cuda
     return cudaSuccess;
 }
 
+// Compact viscous terms (visc_compact): the derivatives of u, v, w, T along
+// every axis by the NOHAP operator (Sec. 3) into Gv, the nodal viscous fluxes
+// in their place, and the NOHAP derivative of each flux along its own axis
+// added into R[1..4].
+template <typename T>
+cudaError_t enqueue_compact_visc(nopcs_ctx *ctx, BoxRes &b, const T *W, T *R, cudaStream_t st)
+{
+    const bool f32 = sizeof(T) == 4;
+    T *G = (T *)b.Gv;
+    const size_t np = (size_t)b.dev.np;
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        Timed t(ctx, st, K_VGRAD);
+        e = launch_line_vgrad<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, b.dev, W, G + 4 * a * np, st);
+    }
+    if (e != cudaSuccess) return e;
+    {
+        Timed t(ctx, st, K_VFLUX);
+        e = launch_visc_flux<T>(b.dev, W, G, st);
+    }
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        Timed t(ctx, st, K_VDIV);
+        e = launch_line_vdiv<T>(f32 ? b.dop32[a].dev : b.dop64[a].dev, a, b.dev, G + 4 * a * np, R, st);
+    }
+    return e;
+}
+
+// The rest of a stage after the convective sweeps: the fused viscous, source
+// and RK kernel, or, with compact viscous terms, those terms and then the
+// source and RK kernel.
+template <typename T>
+cudaError_t enqueue_visc_stage(nopcs_ctx *ctx, BoxRes &b, const T *W, T *R, int stage, const StageRegs<T> &g,
+                               cudaStream_t st)
+{
+    if (!b.d.visc_compact) {
+        Timed t(ctx, st, K_VISC);
+        return launch_visc_update<T>(b.dev, W, R, stage, g, st);
+    }
+    cudaError_t e = enqueue_compact_visc<T>(ctx, b, W, R, st);
+    if (e != cudaSuccess) return e;
+    Timed t(ctx, st, K_SRC);
+    return launch_source_update<T>(b.dev, W, R, stage, g, st);
+}
+
 // FP64 form: stage s of classical RK4 from the FP64 stage state Qin
 cudaError_t enqueue_stage_fp64(nopcs_ctx *ctx, BoxRes &b, int stage, const double *Qin, double *Rout,
                                cudaStream_t st)
@@ -534,10 +596,7 @@ cudaError_t enqueue_stage_fp64(nopcs_ctx *ctx, BoxRes &b, int stage, const doubl
     g.acc = b.acc();
     g.Qout = stage == 4 ? b.Qn() : b.Qs();
     g.Rout = Rout;
-    {
-        Timed t(ctx, st, K_VISC);
-        e = launch_visc_update<double>(x, W, R, stage, g, st);
-    }
+    e = enqueue_visc_stage<double>(ctx, b, W, R, stage, g, st);
     if (e != cudaSuccess || stage == 0) return e;
     Timed t(ctx, st, K_BC);
     return launch_wall_bc(x, g.Qout, nullptr, nullptr, nullptr, st);
@@ -557,10 +616,7 @@ cudaError_t enqueue_stage_mixed(nopcs_ctx *ctx, BoxRes &b, int stage, cudaStream
     g.Kacc = b.Km();
     g.Dn = b.Dn();
     g.Wn = Wout;
-    {
-        Timed t(ctx, st, K_VISC);
-        e = launch_visc_update<float>(x, Win, b.Rm(), stage, g, st);
-    }
+    e = enqueue_visc_stage<float>(ctx, b, Win, b.Rm(), stage, g, st);
     if (e != cudaSuccess) return e;
     Timed t(ctx, st, K_BC);
     if (stage < 4) return launch_wall_bc(x, nullptr, nullptr, nullptr, Wout, st);
@@ -578,7 +634,7 @@ cudaError_t enqueue_rhs_only(nopcs_ctx *ctx, BoxRes &b, const double *q, void *r
     if ((e = enqueue_rhs_sweeps<float>(ctx, b, W, b.Rm(), st)) != cudaSuccess) return e;
     StageRegs<float> g;
     g.Rout = (float *)r;
-    return launch_visc_update<float>(b.dev, W, b.Rm(), 0, g, st);
+    return enqueue_visc_stage<float>(ctx, b, W, b.Rm(), 0, g, st);
 }
 
 cudaError_t enqueue_filter(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)

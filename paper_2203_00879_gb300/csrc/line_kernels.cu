@@ -18,6 +18,11 @@
 // (transposed again for x).  Sub-domains are independent, so no block waits
 // for another.  (The single-field derivative along x keeps its whole staged
 // tile and takes the end values from it.)
+//
+// Modes: FIELD / FIELD2 one field; FLUX the five inviscid fluxes along the
+// axis from the stage primitives, into R; FILTER five state fields; VGRAD and
+// VDIV the compact viscous terms -- the derivatives of u, v, w, T, and those
+// of the four viscous-flux components along the axis, added into R[1..4].
 #include "line_solve.cuh"
 
 namespace nopcs {
@@ -31,13 +36,17 @@ struct LineArgs {
     int rw;         // solve-window capacity (op.max_win): tile rows along y, z
     // one base pointer per field, so a node is one 32-bit index away from a
     // kernel parameter (fields hold < 2^31 points)
-    const T *in[6]; // FIELD: f; FLUX: W (6 fields); FILTER: Q (5 fields)
-    T *out[5];      // FIELD: df; FLUX: R (5 fields); FILTER: Qout (5 fields)
-    T scale;        // 1/h for FIELD and FLUX
+    const T *in[6]; // FIELD: f; FLUX: W (6 fields); FILTER: Q (5 fields);
+                    // VGRAD: W (first 5 fields); VDIV: 4 flux fields
+    T *out[5];      // FIELD: df; FLUX: R (5 fields); FILTER: Qout (5 fields);
+                    // VGRAD: 4 gradient fields; VDIV: R[1..4]
+    T scale;        // 1/h for FIELD, FLUX, VGRAD and VDIV
     int first;      // FLUX: store (1) or subtract (0)
     int ga;         // gravity axis
-    const T *b0;    // FLUX: rho_b, FILTER: rho_b
-    const T *b1;    // FLUX: H_b,   FILTER: E_b
+    const T *b0;    // FLUX: rho_b, FILTER: rho_b, VGRAD: T_b (FP32) / rho_b (FP64)
+    const T *b1;    // FLUX: H_b,   FILTER: E_b,   VGRAD: 1/p_b (FP32) / p_b (FP64)
+    const T *b2;    // VGRAD: 1/rho_b (FP32)
+    T gm2;          // VGRAD: gamma M^2 (FP64)
 };
 
 template <typename T, int MODE, int AXIS>
@@ -45,8 +54,9 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr bool SINGLE = MODE == MODE_FIELD || MODE == MODE_FIELD2;  // one field in, one out
-    constexpr int NF = SINGLE ? 1 : 5;
-    constexpr int NIN = SINGLE ? 1 : (MODE == MODE_FLUX ? 6 : 5);
+    constexpr bool VISC = MODE == MODE_VGRAD || MODE == MODE_VDIV;      // four fields out
+    constexpr int NF = SINGLE ? 1 : (VISC ? 4 : 5);
+    constexpr int NIN = SINGLE ? 1 : (MODE == MODE_FLUX ? 6 : (MODE == MODE_VDIV ? 4 : 5));
     constexpr int U = 4;                               // loads in flight per thread and pass
     // STREAM: the end-row dot products are summed while staging and only the
     // solve window is kept (four blocks per SM instead of three for the flux
@@ -163,6 +173,22 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                         val[2] = m * vv + (AXIS == 1 ? pp : T(0));
                         val[3] = m * ww + (AXIS == 2 ? pp : T(0));
                         val[4] = H * ud;
+                    } else if constexpr (MODE == MODE_VGRAD) {
+                        // u, v, w and T = gamma M^2 p / rho of the stage state
+                        const int gk = gsel == 0 ? g : gl;
+                        val[0] = v[u][1];
+                        val[1] = v[u][2];
+                        val[2] = v[u][3];
+                        if constexpr (sizeof(T) == 4) {
+                            // T_b (1 + p'/p_b) / (1 + rho'/rho_b) on the deviations
+                            const T rr = v[u][0] * a.b2[gk];
+                            val[3] = a.b0[gk] + __fdividef(a.b0[gk] * (v[u][4] * a.b1[gk] - rr), 1.0f + rr);
+                        } else {
+                            val[3] = a.gm2 * (a.b1[gk] + v[u][4]) / (a.b0[gk] + v[u][0]);
+                        }
+                    } else if constexpr (MODE == MODE_VDIV) {
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) val[f] = v[u][f];
                     } else {  // FILTER on Q - base (no base tables: the input is a deviation already)
                         const int gk = gsel == 0 ? g : gl;
                         val[0] = a.b0 ? v[u][0] - a.b0[gk] : v[u][0];
@@ -286,6 +312,13 @@ __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
                             else
                                 atomicAdd(&a.out[f][o], v);
                         }
+                    } else if constexpr (MODE == MODE_VGRAD) {
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) a.out[f][o] = src[f * fs] * a.scale;
+                    } else if constexpr (MODE == MODE_VDIV) {
+                        // one addition per element and sweep, as for the flux
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) atomicAdd(&a.out[f][o], src[f * fs] * a.scale);
                     } else {
                         const int gk = gsel == 0 ? s + rr : gl;
                         a.out[0][o] = a.b0 ? src[0] + a.b0[gk] : src[0];
@@ -315,7 +348,7 @@ template <typename T, int MODE, int AXIS>
 cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cudaStream_t st)
 {
     constexpr bool SINGLE = MODE == MODE_FIELD || MODE == MODE_FIELD2;
-    constexpr int NF = SINGLE ? 1 : 5;
+    constexpr int NF = SINGLE ? 1 : (MODE == MODE_VGRAD || MODE == MODE_VDIV ? 4 : 5);
     a.rt = op.max_tile;
     a.rw = op.max_win;
     const int rows = (AXIS != 0 || !SINGLE) ? a.rw : a.rt;
@@ -379,7 +412,13 @@ cudaError_t init_line_kernels()
         allow_smem<float, MODE_FILTER, 1>(),   allow_smem<float, MODE_FILTER, 2>(),
         allow_smem<float, MODE_FIELD2, 0>(),   allow_smem<float, MODE_FIELD2, 1>(),
         allow_smem<float, MODE_FIELD2, 2>(),   allow_smem<double, MODE_FIELD2, 0>(),
-        allow_smem<double, MODE_FIELD2, 1>(),  allow_smem<double, MODE_FIELD2, 2>()};
+        allow_smem<double, MODE_FIELD2, 1>(),  allow_smem<double, MODE_FIELD2, 2>(),
+        allow_smem<float, MODE_VGRAD, 0>(),    allow_smem<float, MODE_VGRAD, 1>(),
+        allow_smem<float, MODE_VGRAD, 2>(),    allow_smem<double, MODE_VGRAD, 0>(),
+        allow_smem<double, MODE_VGRAD, 1>(),   allow_smem<double, MODE_VGRAD, 2>(),
+        allow_smem<float, MODE_VDIV, 0>(),     allow_smem<float, MODE_VDIV, 1>(),
+        allow_smem<float, MODE_VDIV, 2>(),     allow_smem<double, MODE_VDIV, 0>(),
+        allow_smem<double, MODE_VDIV, 1>(),    allow_smem<double, MODE_VDIV, 2>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -463,6 +502,49 @@ cudaError_t launch_line_field2(const LineOpDev &op, int axis, const int n[3], co
     return launch_any<T, MODE_FIELD2>(op, axis, a, sizeof(T) == 4 ? 64 : 32, st);
 }
 
+template <typename T>
+cudaError_t launch_line_vgrad(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *G, cudaStream_t st)
+{
+    LineArgs<T> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
+    for (int k = 0; k < 5; ++k) a.in[k] = W + (size_t)k * bx.np;
+    for (int k = 0; k < 4; ++k) a.out[k] = G + (size_t)k * bx.np;
+    a.scale = (T)bx.inv_h[axis];
+    a.ga = bx.ga;
+    if constexpr (sizeof(T) == 8) {
+        a.b0 = (const T *)bx.rho_b64;
+        a.b1 = (const T *)bx.p_b64;
+        a.gm2 = (T)bx.gm2;
+    } else {
+        a.b0 = (const T *)bx.T_b32;
+        a.b1 = (const T *)bx.ip_b32;
+        a.b2 = (const T *)bx.ir_b32;
+    }
+    return launch_any<T, MODE_VGRAD>(op, axis, a, sizeof(T) == 4 ? 32 : 16, st);
+}
+
+template <typename T>
+cudaError_t launch_line_vdiv(const LineOpDev &op, int axis, const BoxDev &bx, const T *F, T *R, cudaStream_t st)
+{
+    LineArgs<T> a{};
+    for (int d = 0; d < 3; ++d) a.n[d] = bx.n[d];
+    for (int k = 0; k < 4; ++k) {
+        a.in[k] = F + (size_t)k * bx.np;
+        a.out[k] = R + (size_t)(1 + k) * bx.np;
+    }
+    a.scale = (T)bx.inv_h[axis];
+    a.ga = bx.ga;
+    return launch_any<T, MODE_VDIV>(op, axis, a, sizeof(T) == 4 ? 32 : 16, st);
+}
+
+template cudaError_t launch_line_vgrad<float>(const LineOpDev &, int, const BoxDev &, const float *, float *,
+                                              cudaStream_t);
+template cudaError_t launch_line_vgrad<double>(const LineOpDev &, int, const BoxDev &, const double *, double *,
+                                               cudaStream_t);
+template cudaError_t launch_line_vdiv<float>(const LineOpDev &, int, const BoxDev &, const float *, float *,
+                                             cudaStream_t);
+template cudaError_t launch_line_vdiv<double>(const LineOpDev &, int, const BoxDev &, const double *, double *,
+                                              cudaStream_t);
 template cudaError_t launch_line_field2<float>(const LineOpDev &, int, const int *, const float *, float *, double,
                                                cudaStream_t);
 template cudaError_t launch_line_field2<double>(const LineOpDev &, int, const int *, const double *, double *,

@@ -16,7 +16,9 @@ namespace nopcs {
 // side like the filter's, explicit wall rows like the derivative's)
 enum LineKind { KIND_DERIV = 0, KIND_FILTER = 1, KIND_D2 = 2 };
 // MODE_FIELD2: one field through a KIND_D2 operator
-enum LineMode { MODE_FIELD = 0, MODE_FLUX = 1, MODE_FILTER = 2, MODE_FIELD2 = 3 };
+// MODE_VGRAD: the derivatives of u, v, w, T (from the six stage primitives)
+// MODE_VDIV: the derivatives of four viscous-flux fields, added into R[1..4]
+enum LineMode { MODE_FIELD = 0, MODE_FLUX = 1, MODE_FILTER = 2, MODE_FIELD2 = 3, MODE_VGRAD = 4, MODE_VDIV = 5 };
 
 // Per-sub-domain record of a line operator (ints, device array of nsub * SUB_REC).
 //   [0] s, [1] e            sub-domain rows (inclusive)
@@ -175,6 +177,13 @@ cudaError_t launch_line_field2(const LineOpDev &op, int axis, const int n[3], co
 template <typename T>
 cudaError_t launch_line_flux(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *R,
                              int first, cudaStream_t st, int lines = 0);
+// Compact viscous terms.  VGRAD: G[q] = L(prim_q(W)) / h for q = u, v, w, T
+// (4 fields at G, np apart).  VDIV: R[1 + c] += L(F[c]) / h for the 4 fields
+// of F (R: the base of the 5 right-hand-side fields).
+template <typename T>
+cudaError_t launch_line_vgrad(const LineOpDev &op, int axis, const BoxDev &bx, const T *W, T *G, cudaStream_t st);
+template <typename T>
+cudaError_t launch_line_vdiv(const LineOpDev &op, int axis, const BoxDev &bx, const T *F, T *R, cudaStream_t st);
 // Plane diagnostics (plane_kernels.cu): what 0 disturbance pressure, 1 the
 // nine vorticity-transport terms.
 cudaError_t launch_plane_fields(const BoxDev &bx, const double *Q, int axis, int index, int what, double *out,
@@ -210,6 +219,17 @@ struct StageRegs {
 template <typename T>
 cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
                                cudaStream_t st);
+// Compact viscous terms: G holds 12 fields, field 4 d + q the derivative along
+// d of primitive q (u, v, w, T); each node's gradients are replaced in place
+// by its viscous fluxes, field 4 d + c component c (x-, y-, z-momentum,
+// energy) of the flux along d.
+template <typename T>
+cudaError_t launch_visc_flux(const BoxDev &bx, const T *W, T *G, cudaStream_t st);
+// Gravity source, no-slip walls and the RK stage of launch_visc_update,
+// without its viscous terms (R already holds them).
+template <typename T>
+cudaError_t launch_source_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
+                                 cudaStream_t st);
 
 // ---- launchers (rk_kernels.cu) ---------------------------------------------
 // W from the FP64 state; Dn (mixed form, optional): deviation from the base.

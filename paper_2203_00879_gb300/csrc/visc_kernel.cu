@@ -59,6 +59,20 @@ struct VArgs {
     float gm1;                            // gamma - 1
 };
 
+// T = gamma M^2 p / rho of a stage state from its primitives W0 = rho - rho_b
+// and W4 = p - p_b at gravity coordinate kg (FP32: T_b (1 + p'/p_b) /
+// (1 + rho'/rho_b), which keeps the deviations' digits)
+template <typename T>
+__device__ __forceinline__ T node_temperature(const VArgs<T> &a, int kg, T w0, T w4)
+{
+    if constexpr (sizeof(T) == 4) {
+        const float rr = w0 * a.ir_b[kg];
+        return a.T_b[kg] + __fdividef(a.T_b[kg] * (w4 * a.ip_b[kg] - rr), 1.0f + rr);
+    } else {
+        return a.gm2 * (a.p_b[kg] + w4) / (a.rho_b[kg] + w0);
+    }
+}
+
 template <typename T>
 struct Ring {
     T *s;
@@ -121,12 +135,7 @@ struct PlaneLoad {
                 uu = u[t];
                 vv = v[t];
                 ww = w[t];
-                if constexpr (sizeof(T) == 4) {
-                    const float rr = w0[t] * a.ir_b[kg];
-                    tt = a.T_b[kg] + __fdividef(a.T_b[kg] * (w4[t] * a.ip_b[kg] - rr), 1.0f + rr);
-                } else {
-                    tt = a.gm2 * (a.p_b[kg] + w4[t]) / (a.rho_b[kg] + w0[t]);
-                }
+                tt = node_temperature(a, kg, w0[t], w4[t]);
             }
             T *p = rg.s + (size_t)(z % RING) * NPF * PLANE + idx;
             p[0] = uu;
@@ -294,6 +303,47 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, int p, int k
         for (int k = 0; k < 5; ++k) a.Dn[k][p] = D[k];
     }
     prim_from_dev(a, p, kg, D);
+}
+
+// Gravity source (Eq. ge8a), no-slip walls and the RK4 stage at node p, whose
+// right-hand side r holds every other term.  w0 = rho - rho_b, ug = the
+// velocity along gravity; kd, dn (mixed form) = the node's K and D_n.
+template <typename T>
+__device__ __forceinline__ void source_and_stage(const VArgs<T> &a, int p, int kg, bool wall, T w0, T ug, T r[5],
+                                                 const float kd[5], const float dn[5])
+{
+    const T rho = a.rho_b[kg] + w0;
+    const T sg = w0 * a.g;
+    if (a.ga == 0) r[1] -= sg;
+    if (a.ga == 1) r[2] -= sg;
+    if (a.ga == 2) r[3] -= sg;
+    r[4] -= rho * ug * a.g;
+    // no-slip walls
+    if (wall) r[1] = r[2] = r[3] = 0;
+    if (a.stage == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a.Rout[k][p] = r[k];
+    } else if constexpr (sizeof(T) == 4) {
+        mixed_update(a, p, kg, r, kd, dn);
+    } else {
+        // classical RK4: acc collects Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
+        const double bw = (a.stage == 1 || a.stage == 4) ? a.dt / 6.0 : a.dt / 3.0;
+        const double cw = a.stage == 3 ? a.dt : 0.5 * a.dt;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const double rk = (double)r[k];
+            if (a.stage == 1) {
+                const double q = a.Qn[k][p];
+                a.acc[k][p] = q + bw * rk;
+                a.Qout[k][p] = q + cw * rk;
+            } else if (a.stage < 4) {
+                a.acc[k][p] = a.acc[k][p] + bw * rk;
+                a.Qout[k][p] = a.Qn[k][p] + cw * rk;
+            } else {
+                a.Qout[k][p] = a.acc[k][p] + bw * rk;
+            }
+        }
+    }
 }
 
 template <typename T, bool EDGE>
@@ -484,41 +534,9 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
                            GV[saa * 4 * TY * TX + gi]) * ihz;
                 r[1 + k] += dvx + dvy + dvz;
             }
-            // gravity source, Eq. ge8a
             const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : o);
-            const T rho = a.rho_b[kg] + w0;
-            const T ug = rg.at(a.ga, x, y, o);
-            const T sg = w0 * a.g;
-            if (a.ga == 0) r[1] -= sg;
-            if (a.ga == 1) r[2] -= sg;
-            if (a.ga == 2) r[3] -= sg;
-            r[4] -= rho * ug * a.g;
-            // no-slip walls
-            if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || o == 0 || o == nz - 1) r[1] = r[2] = r[3] = 0;
-            if (a.stage == 0) {
-#pragma unroll
-                for (int k = 0; k < 5; ++k) a.Rout[k][p] = r[k];
-            } else if constexpr (sizeof(T) == 4) {
-                mixed_update(a, p, kg, r, kd, dn);
-            } else {
-                // classical RK4: acc collects Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
-                const double bw = (a.stage == 1 || a.stage == 4) ? a.dt / 6.0 : a.dt / 3.0;
-                const double cw = a.stage == 3 ? a.dt : 0.5 * a.dt;
-#pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const double rk = (double)r[k];
-                    if (a.stage == 1) {
-                        const double q = a.Qn[k][p];
-                        a.acc[k][p] = q + bw * rk;
-                        a.Qout[k][p] = q + cw * rk;
-                    } else if (a.stage < 4) {
-                        a.acc[k][p] = a.acc[k][p] + bw * rk;
-                        a.Qout[k][p] = a.Qn[k][p] + cw * rk;
-                    } else {
-                        a.Qout[k][p] = a.acc[k][p] + bw * rk;
-                    }
-                }
-            }
+            const bool wall = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || o == 0 || o == nz - 1;
+            source_and_stage(a, p, kg, wall, w0, rg.at(a.ga, x, y, o), r, kd, dn);
         }
         if (next) {
             pl.finish(a, rg);
@@ -545,6 +563,77 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 1024 : 512) / (TX * 
         visc_rk_body<T, false>(a, smraw);
 }
 
+// Compact viscous terms, step 2 of 3: the nodal viscous fluxes from the
+// gradients that the VGRAD sweeps left in G, written over them in place
+// (field 4 d + q = d(prim q)/dx_d in, field 4 d + c = component c of the flux
+// along d out; a node's twelve values are read before any is written).
+template <typename T>
+__global__ void __launch_bounds__(256) visc_flux_kernel(const VArgs<T> a, T *__restrict__ G)
+{
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const size_t np = (size_t)a.np;
+    for (long long q = blockIdx.x * blockDim.x + threadIdx.x; q < a.np; q += gridDim.x * blockDim.x) {
+        const int p = (int)q;  // boxes hold < 2^31 points
+        T g[3][4];  // g[d][q] = d(prim q)/dx_d, prim = u, v, w, T
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[d][q] = G[(4 * d + q) * np + p];
+        const int x = p % nx, y = (p / nx) % ny, z = p / (nx * ny);
+        const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : z);
+        const T u = a.W[1][p], v = a.W[2][p], w = a.W[3][p];
+        T mu, mub;
+        visc_coeffs(a, node_temperature(a, kg, a.W[0][p], a.W[4][p]), mu, mub);
+        const T k43 = (T(4) / T(3) * mu + mub) * a.iRe, k23 = (T(-2) / T(3) * mu + mub) * a.iRe, ks = mu * a.iRe;
+        // stress tensor, Eqs. ge19, bv1-bv3 (d u_i / d x_j = g[j][i])
+        const T txx = k43 * g[0][0] + k23 * (g[1][1] + g[2][2]);
+        const T tyy = k43 * g[1][1] + k23 * (g[0][0] + g[2][2]);
+        const T tzz = k43 * g[2][2] + k23 * (g[0][0] + g[1][1]);
+        const T txy = ks * (g[1][0] + g[0][1]);
+        const T txz = ks * (g[2][0] + g[0][2]);
+        const T tyz = ks * (g[2][1] + g[1][2]);
+        // heat flux, Eq. ge20; its normal component is zero on an adiabatic wall
+        const T mk = -mu * a.kq;
+        const T qx = (x == 0 || x == nx - 1) ? T(0) : mk * g[0][3];
+        const T qy = (y == 0 || y == ny - 1) ? T(0) : mk * g[1][3];
+        const T qz = (z == 0 || z == nz - 1) ? T(0) : mk * g[2][3];
+        const T f[12] = {txx, txy, txz, u * txx + v * txy + w * txz - qx,
+                         txy, tyy, tyz, u * txy + v * tyy + w * tyz - qy,
+                         txz, tyz, tzz, u * txz + v * tyz + w * tzz - qz};
+#pragma unroll
+        for (int k = 0; k < 12; ++k) G[k * np + p] = f[k];
+    }
+}
+
+// Compact viscous terms, step 3 of 3 (after the VDIV sweeps added the
+// divergence into R): gravity source, no-slip walls and the RK stage.
+template <typename T>
+__global__ void __launch_bounds__(256) source_rk_kernel(const VArgs<T> a)
+{
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    for (long long q = blockIdx.x * blockDim.x + threadIdx.x; q < a.np; q += gridDim.x * blockDim.x) {
+        const int p = (int)q;  // boxes hold < 2^31 points
+        T r[5];
+        float kd[5], dn[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = a.R[k][p];
+        if constexpr (sizeof(T) == 4) {
+            if (a.stage >= 2) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) kd[k] = a.Kacc[k][p];
+            }
+            if (a.stage >= 1 && a.stage <= 3) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) dn[k] = a.Dn[k][p];
+            }
+        }
+        const int x = p % nx, y = (p / nx) % ny, z = p / (nx * ny);
+        const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : z);
+        const bool wall = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+        source_and_stage(a, p, kg, wall, a.W[0][p], a.W[1 + a.ga][p], r, kd, dn);
+    }
+}
+
 template <typename T>
 size_t ring_bytes()
 {
@@ -552,20 +641,8 @@ size_t ring_bytes()
            sizeof(T);
 }
 
-}  // namespace
-
-cudaError_t init_visc_kernels()
-{
-    cudaError_t e = cudaFuncSetAttribute(visc_rk_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ring_bytes<float>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(visc_rk_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ring_bytes<double>());
-}
-
 template <typename T>
-cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
-                               cudaStream_t st)
+VArgs<T> make_vargs(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g)
 {
     VArgs<T> a{};
     for (int d = 0; d < 3; ++d) {
@@ -608,6 +685,33 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
     a.rho_b64 = bx.rho_b64;
     a.E_b64 = bx.E_b64;
     a.gm1 = (float)(bx.gamma - 1.0);
+    return a;
+}
+
+// pointwise kernels: a grid of 8 blocks of 256 per SM striding over the box
+unsigned pointwise_blocks(long long np)
+{
+    long long b = (np + 255) / 256;
+    if (b > 152LL * 8) b = 152LL * 8;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t init_visc_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(visc_rk_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ring_bytes<float>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(visc_rk_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ring_bytes<double>());
+}
+
+template <typename T>
+cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
+                               cudaStream_t st)
+{
+    VArgs<T> a = make_vargs(bx, W, R, stage, g);
     const int gx = (bx.n[0] + TX - 1) / TX, gy = (bx.n[1] + TY - 1) / TY;
     // z chunk: enough blocks for the whole GPU, at least 8 planes per block
     const long long want = 152LL * 8;
@@ -621,6 +725,29 @@ cudaError_t launch_visc_update(const BoxDev &bx, const T *W, const T *R, int sta
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_visc_flux(const BoxDev &bx, const T *W, T *G, cudaStream_t st)
+{
+    const VArgs<T> a = make_vargs(bx, W, (const T *)nullptr, 0, StageRegs<T>{});
+    visc_flux_kernel<T><<<pointwise_blocks(bx.np), 256, 0, st>>>(a, G);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_source_update(const BoxDev &bx, const T *W, const T *R, int stage, const StageRegs<T> &g,
+                                 cudaStream_t st)
+{
+    const VArgs<T> a = make_vargs(bx, W, R, stage, g);
+    source_rk_kernel<T><<<pointwise_blocks(bx.np), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_visc_flux<float>(const BoxDev &, const float *, float *, cudaStream_t);
+template cudaError_t launch_visc_flux<double>(const BoxDev &, const double *, double *, cudaStream_t);
+template cudaError_t launch_source_update<float>(const BoxDev &, const float *, const float *, int,
+                                                 const StageRegs<float> &, cudaStream_t);
+template cudaError_t launch_source_update<double>(const BoxDev &, const double *, const double *, int,
+                                                  const StageRegs<double> &, cudaStream_t);
 template cudaError_t launch_visc_update<float>(const BoxDev &, const float *, const float *, int,
                                               const StageRegs<float> &, cudaStream_t);
 template cudaError_t launch_visc_update<double>(const BoxDev &, const double *, const double *, int,

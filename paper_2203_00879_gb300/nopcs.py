@@ -16,7 +16,7 @@ NOPCS_OK, NOPCS_EINVAL, NOPCS_ENOMEM, NOPCS_ECUDA, NOPCS_EUNSTABLE, NOPCS_ETIMEO
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "EUNSUPPORTED"]
 NOPCS_FP64, NOPCS_MIXED = 0, 1
 NOPCS_FORM_AUTO, NOPCS_FORM_THOMAS, NOPCS_FORM_GEMM_3XTF32, NOPCS_FORM_GEMM_BF16X3, NOPCS_FORM_BANDED = range(5)
-NOPCS_NUM_KERNELS = 8
+NOPCS_NUM_KERNELS = 12
 
 
 class NopcsError(RuntimeError):
@@ -33,7 +33,7 @@ class nopcs_box_desc(C.Structure):
                 ("mu_s_si", C.c_double), ("Ts_kelvin", C.c_double), ("T_upper", C.c_double),
                 ("T_lower", C.c_double), ("g", C.c_double), ("dt", C.c_double),
                 ("filter_every", C.c_int), ("filter_alpha", C.c_double), ("base_subtract", C.c_int),
-                ("seed", C.c_ulonglong), ("perturb_amp", C.c_double)]
+                ("seed", C.c_ulonglong), ("perturb_amp", C.c_double), ("visc_compact", C.c_int)]
 
 
 class nopcs_diag(C.Structure):

@@ -179,7 +179,9 @@ def test_deterministic_and_graph_equals_direct():
                 assert t["sweep_x"][1] == 20 and t["filter"][1] == 2
                 # the mixed form recovers primitives inside the stage kernels:
                 # no separate prep launch during steps
-                assert all(v[0] > 0 for k, v in t.items() if k not in ("diagnostics", "prep"))
+                compact_only = ("visc_grad", "visc_flux", "visc_div", "source_rk_update")
+                assert all(v[0] > 0 for k, v in t.items() if k not in ("diagnostics", "prep") + compact_only)
+                assert all(t[k][1] == 0 for k in compact_only)
         finally:
             N.nopcs_destroy(ctx)
     assert np.array_equal(outs[0], outs[1])

@@ -37,6 +37,13 @@ ALG_BYTES_MIXED = {
     # stage average of W + R + Dn (+ K) in, K + W' out; stage 4 also Q_n in/out and Dn out
     "visc_rk_update": (108 + 128 + 128 + 188) / 4.0,
     "filter": 3 * 80,                  # three sweeps, each read+write Q
+    # compact viscous terms (visc_compact): per launch of each kind
+    "visc_grad": 20 + 16,              # read rho', u, v, w, p'; write 4 gradients
+    "visc_flux": 48 + 20 + 48,         # read 12 gradients and 5 primitives, write 12 fluxes
+    "visc_div": 16 + 32,               # read 4 fluxes; reduction adds into R[1..4] (read + write)
+    # visc_rk_update without the viscous terms: W0 and the velocity along gravity
+    # instead of the five primitives the viscous stencils need
+    "source_rk_update": (92 + 112 + 112 + 172) / 4.0,
 }
 ALG_BYTES_FP64 = {
     "prep": 40 + 48, "sweep_x": 48 + 40, "sweep_y": 48 + 80, "sweep_z": 48 + 80,
@@ -54,6 +61,9 @@ def parse():
     ap.add_argument("--sub-n", type=int, default=64)
     ap.add_argument("--fp64-n", type=int, default=1024, help="grid of the FP64-form comparison (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--compact-n", type=int, default=1024,
+                    help="grid of the compact-viscous-term measurement, mixed form (0: skip)")
+    ap.add_argument("--compact-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-n", type=int, default=128, help="oracle sample grid for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle sample steps for the CPU baseline")
@@ -458,6 +468,38 @@ def main():
                 "ms_per_step": m64 / args.fp64_steps, "mixed_over_fp64": value / v64}
         N.nopcs_destroy(ctx)
 
+    # mixed form with compact viscous terms (NOHAP gradients and divergence)
+    compact = None
+    if args.compact_n > 0:
+        nc = args.compact_n
+        pc = box(nc, args.sub_n, seed=1 + rank, visc_compact=1)
+        ctx = N.nopcs_init([pc], prec=N.NOPCS_MIXED, stream=st)
+        N.nopcs_rk_step(ctx, 1)
+        N.nopcs_set_profiling(ctx, True)
+        N.nopcs_profile_read(ctx, reset=True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        N.nopcs_rk_step(ctx, args.compact_steps)
+        e1.record(stream)
+        barrier()
+        mc = rank_max(e0.elapsed_time(e1))
+        pr = N.nopcs_profile_read(ctx, reset=True)
+        N.nopcs_destroy(ctx)
+        ptc = float(nc) ** 3
+        kc = {}
+        for k, (kms, kn) in pr.items():
+            if not kn:
+                continue
+            ent = {"ms_per_launch": kms / kn, "launches": kn}
+            if k in ALG_BYTES_MIXED and k != "filter":
+                gbs = ALG_BYTES_MIXED[k] * ptc / (kms / kn * 1e-3) / 1e9
+                ent.update(alg_bytes_per_point=ALG_BYTES_MIXED[k], achieved_gbs=gbs, frac=gbs / hbm)
+            kc[k] = ent
+        compact = {"value": world * ptc * 4 * args.compact_steps / (mc * 1e-3), "unit": UNIT, "grid": [nc] * 3,
+                   "steps": args.compact_steps, "ms_per_step": mc / args.compact_steps, "kernels": kc,
+                   "explicit_over_compact": value / (world * ptc * 4 * args.compact_steps / (mc * 1e-3))}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, dt, cores = run_cpu_oracle(args.cpu_n, args.cpu_steps)
@@ -482,6 +524,7 @@ def main():
             "gpu_launches": gpu_launches,
             "e2e": e2e,
             "fp64_form": fp64,
+            "compact_viscous_form": compact,
             "cpu_baseline": cpu,
             "clocks": clk,
             "diagnostics": {"step": diag["step"], "max_speed": diag["max_speed"], "max_dp": diag["max_dp"]},

@@ -1,0 +1,114 @@
+"""Parity of one right-hand side at the benchmark's full size (1024^3, mixed
+form, sub-domains of 64: the launch configuration bench.py times) with the
+FP64 oracle.
+
+The oracle cannot hold a 1024^3 box, so the state varies along z (the
+hydrostatic two-temperature base) and along one horizontal axis only.  Every
+derivative across the third axis is then of a constant, which both sides
+take as zero -- exactly in the oracle and in the CUDA path's interior Thomas
+rows and explicit stencils, to FP32 rounding in the CUDA path's sub-domain end
+rows (their taps sum to zero only to rounding) and on the edge rows of the
+viscous kernel's tiles (there the two neighbouring viscous fluxes come from the
+tile and from the halo code, which may round differently) -- so on rows near
+sub-domain centres (16 or more rows from an end, where an end value's weight
+has decayed below 1e-5) and inside a tile, the 1024^3 right-hand side equals
+the oracle's on a box five nodes thick along that axis.  Both horizontal axes are covered
+(the x sweep and the y sweep at full line length; z in both), with the
+explicit and with the compact viscous terms; the latter on 1024 x 1024 x 768,
+since its 12 scratch fields and the test's own input and output copies would
+not fit beside a 1024^3 box on one GPU."""
+import numpy as np
+import pytest
+
+import nopcs_synth as S
+import oracle
+from gpu_util import binding, field_rel, stream_ptr
+
+pytestmark = pytest.mark.gpu
+
+N1 = 1024
+SUB = 64
+
+
+def _thin_box(vary, visc_compact, nz):
+    """The oracle's box: N1 along `vary`, nz along z, five nodes along the
+    other horizontal axis, the same spacing as the N1 x N1 x nz box."""
+    h = 1.0 / (N1 - 1)
+    n = [N1, N1, nz]
+    n[1 - vary] = 5
+    length = tuple(h * (v - 1) for v in n)
+    sub = [SUB, SUB, SUB]
+    sub[1 - vary] = 0
+    return S.box_params(tuple(n), sub_n=tuple(sub), length=length, base_subtract=1, perturb_amp=0.0,
+                        visc_compact=visc_compact)
+
+
+def _thin_state(p, vary):
+    """Hydrostatic base plus a seeded perturbation that depends on (vary, z)
+    only: density and energy by 1e-4 relative, velocity 1e-3 uniform."""
+    Q = oracle.Solver(p).initial_state()  # (5, nz, ny, nx)
+    nz = Q.shape[1]
+    plane = nz * N1
+    idx = np.arange(plane, dtype=np.uint64)
+
+    def noise(c):
+        u = 2.0 * S.uniform01(17, idx + np.uint64(c * plane)) - 1.0
+        u = u.reshape(nz, N1)
+        return u[:, None, :] if vary == 0 else u[:, :, None]
+
+    rho = Q[0] * (1 + 1e-4 * noise(0))
+    E0 = Q[4] * (1 + 1e-4 * noise(1))
+    Q[0] = rho
+    for k in range(3):
+        Q[1 + k] = rho * 1e-3 * noise(2 + k)
+    Q[4] = E0 + 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / rho
+    return Q
+
+
+def _no_slip(R):
+    R = R.copy()
+    R[1:4][:, [0, -1]] = 0
+    R[1:4][:, :, [0, -1]] = 0
+    R[1:4][:, :, :, [0, -1]] = 0
+    return R
+
+
+@pytest.mark.parametrize("visc_compact,nz", [(0, N1), (1, 768)])
+def test_rhs_1024_matches_oracle_on_sampled_rows(visc_compact, nz):
+    import torch
+    N = binding()
+    p = S.box_params((N1, N1, nz), sub_n=(SUB, SUB, SUB), base_subtract=1, visc_compact=visc_compact)
+    ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=stream_ptr())
+    try:
+        for vary in (0, 1):
+            pt = _thin_box(vary, visc_compact, nz)
+            Qt = _thin_state(pt, vary)
+            ref = _no_slip(oracle.Solver(pt).rhs(Qt))
+            # the same state, constant along the thin axis, on the N1^3 box
+            if vary == 0:
+                src = torch.from_numpy(np.ascontiguousarray(Qt[:, :, 2:3, :])).cuda()
+            else:
+                src = torch.from_numpy(np.ascontiguousarray(Qt[:, :, :, 2:3])).cuda()
+            q = src.expand(5, nz, N1, N1).contiguous()
+            del src
+            r = torch.empty((5, nz, N1, N1), dtype=torch.float32, device="cuda")
+            N.nopcs_rhs(ctx, 0, q.data_ptr(), r.data_ptr())
+            torch.cuda.synchronize()
+            del q
+            refrow = ref[:, :, 2, :] if vary == 0 else ref[:, :, :, 2]
+            errs = []
+            # rows across y: inside the viscous tiles' 8 rows; across x: inside their 32 columns
+            rows = (36, 548, 996) if vary == 0 else (48, 560, 976)
+            for row in rows:
+                got = (r[:, :, row, :] if vary == 0 else r[:, :, :, row]).cpu().numpy().astype(np.float64)
+                errs.append(field_rel(got, refrow))
+                d = np.abs(got - refrow).reshape(5, -1)
+                print("row", row, "max error at (z, horizontal)",
+                      [np.unravel_index(int(d[k].argmax()), refrow.shape[1:]) for k in range(5)])
+            del r
+            torch.cuda.empty_cache()
+            err = np.max(errs, axis=0)
+            print("vary", vary, "visc_compact", visc_compact, "field-relative", err)
+            assert np.all(err <= 1e-5), (vary, err)  # measured 1.6e-7 .. 2.7e-7
+    finally:
+        N.nopcs_destroy(ctx)

@@ -479,9 +479,11 @@ def main():
         N.nopcs_profile_read(ctx, reset=True)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        profiler_range(True)
         e0.record(stream)
         N.nopcs_rk_step(ctx, args.compact_steps)
         e1.record(stream)
+        profiler_range(False)
         barrier()
         mc = rank_max(e0.elapsed_time(e1))
         pr = N.nopcs_profile_read(ctx, reset=True)

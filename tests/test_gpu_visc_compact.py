@@ -144,3 +144,25 @@ def test_compact_viscous_rest_state():
         assert d["max_speed"] < 1e-10 and d["nonfinite"] == 0
     finally:
         N.nopcs_destroy(ctx)
+
+
+def test_compact_and_explicit_boxes_in_one_context():
+    """A context holding a box with compact viscous terms and one with the
+    paper's explicit ones (one CUDA graph, a branch per box) advances each
+    exactly as a context of its own does."""
+    N = binding()
+    boxes = [S.box_params((24, 20, 30), sub_n=(8, 8, 8), seed=3, Re=300.0, perturb_amp=1e-3, visc_compact=1),
+             S.box_params((17, 33, 21), sub_n=(5, 16, 0), seed=4, T_lower=1.5, perturb_amp=1e-3)]
+    ctx = N.nopcs_init(boxes, prec=N.NOPCS_MIXED, stream=stream_ptr())
+    try:
+        N.nopcs_rk_step(ctx, 3)
+        both = [_state(N, ctx, p, b) for b, p in enumerate(boxes)]
+    finally:
+        N.nopcs_destroy(ctx)
+    for b, p in enumerate(boxes):
+        c1 = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=stream_ptr())
+        try:
+            N.nopcs_rk_step(c1, 3)
+            assert np.array_equal(_state(N, c1, p), both[b])
+        finally:
+            N.nopcs_destroy(c1)

@@ -362,8 +362,10 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     const int z0 = blockIdx.z * a.zc, z1 = min(nz, z0 + a.zc);
     const int tx = (int)(threadIdx.x % TX), ty = (int)(threadIdx.x / TX);
     const int x = rg.x0 + tx, y = rg.y0 + ty;
-    const bool in_dom = x < nx && y < ny;
-    const bool own = in_dom && x >= xs && y >= ys;
+    // a block off the x and y walls (EDGE false) is never shifted back and
+    // owns all its nodes, halo nodes included, inside the box
+    const bool in_dom = !EDGE || (x < nx && y < ny);
+    const bool own = !EDGE || (in_dom && x >= xs && y >= ys);
     // G_v planes are computed in increasing order; ghi is the last one, and
     // the ring holds the GSLOTS planes up to it
     int ghi = -1000;
@@ -447,7 +449,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
             const int side = t / TX, hx = t % TX;
             const int ly = side ? TY : -1;
             const int gx = rg.x0 + hx, gy = rg.y0 + ly;
-            if (gy >= 0 && gy < ny && gx < nx) {
+            if (!EDGE || (gy >= 0 && gy < ny && gx < nx)) {
                 T E[4], F[4];
                 flux_xy(a, stencil_at(hx, ly, 0, o), false, true, E, F);
 #pragma unroll
@@ -458,7 +460,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
             const int side = t / TY, hy = t % TY;
             const int lx = side ? TX : -1;
             const int gx = rg.x0 + lx, gy = rg.y0 + hy;
-            if (gx >= 0 && gx < nx && gy < ny) {
+            if (!EDGE || (gx >= 0 && gx < nx && gy < ny)) {
                 T E[4], F[4];
                 flux_xy(a, stencil_at(lx, hy, 0, o), true, false, E, F);
 #pragma unroll
@@ -514,7 +516,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
                     for (int k = 0; k < 5; ++k) dn[k] = a.Dn[k][p];
                 }
             }
-            const int xm = wall_mode(x, nx), ym = wall_mode(y, ny);
+            const int xm = EDGE ? wall_mode(x, nx) : 0, ym = EDGE ? wall_mode(y, ny) : 0;
             const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
             // slots of G_v planes o-1, o+1, o, o+2, o-2 (GSLOTS = 3)
             const int sa = (o + 2) % GSLOTS, sb = (o + 1) % GSLOTS, s0 = o % GSLOTS;
@@ -548,7 +550,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
                 r[1 + k] += dvx + dvy + dvz;
             }
             const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : o);
-            const bool wall = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || o == 0 || o == nz - 1;
+            const bool wall = (EDGE && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) || o == 0 || o == nz - 1;
             source_and_stage(a, p, kg, wall, w0, rg.at(a.ga, x, y, o), r, kd, dn);
         }
         if (next) {

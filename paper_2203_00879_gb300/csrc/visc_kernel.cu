@@ -73,6 +73,37 @@ __device__ __forceinline__ T node_temperature(const VArgs<T> &a, int kg, T w0, T
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Ask L2 for what the RK update of node p will load: its right-hand side and
+// (mixed form) K, D_n and, in stage 4, Q_n.  Issued a plane ahead, these take
+// the DRAM latency off the update, which runs after the plane's barrier with
+// no registers to spare for loading early (the 64-register cap keeps four
+// blocks per SM).
+template <typename T>
+__device__ __forceinline__ void prefetch_node(const VArgs<T> &a, int p)
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) prefetch_l2(a.R[k] + p);
+    if constexpr (sizeof(T) == 4) {
+        if (a.stage >= 2) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) prefetch_l2(a.Kacc[k] + p);
+        }
+        if (a.stage >= 1 && a.stage <= 3) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) prefetch_l2(a.Dn[k] + p);
+        }
+        if (a.stage == 4) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) prefetch_l2(a.Qn[k] + p);
+        }
+    }
+}
+
 template <typename T>
 struct Ring {
     T *s;
@@ -499,6 +530,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         const int zn = lhi + 1;
         const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
         if (next) pl.issue(a, zn);
+        if (own && o + 1 < z1) prefetch_node(a, x + nx * (y + ny * (o + 1)));
         if (own) {
             const int p = x + nx * (y + ny * o);
             T r[5];

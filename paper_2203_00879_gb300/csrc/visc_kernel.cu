@@ -154,6 +154,20 @@ struct PlaneLoad {
             }
         }
     }
+    // ask L2 for plane zz's primitives of this thread's ring nodes (the plane
+    // after the one being loaded, so its loads find them there)
+    __device__ __forceinline__ void prefetch(const VArgs<T> &a, int zz) const
+    {
+        const int zo = a.n[0] * a.n[1] * zz;
+#pragma unroll
+        for (int t = 0; t < PL_PER_THREAD; ++t) {
+            if (goff[t] >= 0) {
+                const int i = zo + goff[t];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) prefetch_l2(a.W[k] + i);
+            }
+        }
+    }
     __device__ __forceinline__ void finish(const VArgs<T> &a, const Ring<T> &rg) const
     {
 #pragma unroll
@@ -530,6 +544,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         const int zn = lhi + 1;
         const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
         if (next) pl.issue(a, zn);
+        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) pl.prefetch(a, zn + 1);  // the next issue's plane
         if (own && o + 1 < z1) prefetch_node(a, x + nx * (y + ny * (o + 1)));
         if (own) {
             const int p = x + nx * (y + ny * o);

@@ -193,7 +193,7 @@ def run_reference(args):
 def run_deriv_microbench(args):
     """NOHAP first derivative of a seeded 512^3 field (random-phase sines plus
     N(0, 1e-3^2) noise) along x, y, z: Thomas form in FP64 and FP32 and the
-    3xTF32 tensor-core form, sub-domains of 32, 64 and 128, and the banded
+    3xTF32 and BF16x3 tensor-core forms, sub-domains of 32, 64 and 128, and the banded
     explicit form (FP32, no sub-domains).  Each case is timed
     with CUDA events over `steps` calls after `warmup`; the field (0.5-1 GB) is
     larger than L2."""
@@ -209,8 +209,10 @@ def run_deriv_microbench(args):
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             bf16 = float(json.load(fh)["bf16_tflops"])
         tf32_peak, tf32_kind = bf16 * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16 ratio"
+        bf16_peak = bf16
     except Exception:
         tf32_peak, tf32_kind = 1900.0 * 1.1 / 2.25, "fallback"
+        bf16_peak = 1900.0
     st = torch.cuda.current_stream()
     px, py, pz = [torch.from_numpy(v).cuda() for v in S.sine_profiles((n, n, n), kmax=64, seed=7)]
     g = torch.Generator(device="cuda").manual_seed(11)
@@ -220,7 +222,8 @@ def run_deriv_microbench(args):
     rows = []
     for sub_n in (32, 64, 128):
         p = box(n, sub_n, perturb_amp=0.0)
-        forms = [("thomas", N.NOPCS_FORM_THOMAS), ("gemm_3xtf32", N.NOPCS_FORM_GEMM_3XTF32)]
+        forms = [("thomas", N.NOPCS_FORM_THOMAS), ("gemm_3xtf32", N.NOPCS_FORM_GEMM_3XTF32),
+                 ("gemm_bf16x3", N.NOPCS_FORM_GEMM_BF16X3)]
         if sub_n == 64:  # the banded form has no sub-domains: timed once
             forms.append(("banded", N.NOPCS_FORM_BANDED))
         for form_name, form in forms:
@@ -251,10 +254,16 @@ def run_deriv_microbench(args):
                         # 49 FP32 FMAs per point (the interior stencil)
                         row["sub_n"] = None
                         row["fp32_tflops"] = 2.0 * 49 * n ** 3 / (ms * 1e-3) / 1e12
-                    elif form_name != "thomas":
+                    elif form_name == "gemm_3xtf32":
+                        # three TF32 products of 2 flops per window point
                         kpad = (sub_n + 48 + 7) // 8 * 8
                         tflops = 6.0 * kpad * n ** 3 / (ms * 1e-3) / 1e12
                         row.update({"tensor_tflops": tflops, "tensor_frac": tflops / tf32_peak})
+                    elif form_name == "gemm_bf16x3":
+                        # six BF16 products of 2 flops per window point
+                        kpad = (sub_n + 48 + 15) // 16 * 16
+                        tflops = 12.0 * kpad * n ** 3 / (ms * 1e-3) / 1e12
+                        row.update({"tensor_tflops": tflops, "tensor_frac": tflops / bf16_peak})
                     rows.append(row)
             N.nopcs_destroy(ctx)
     best = max((r for r in rows if r.get("dtype") == "f32"), key=lambda r: r["points_per_s"])
@@ -265,7 +274,8 @@ def run_deriv_microbench(args):
             "config": {"workload": "seeded 512^3 sine+noise field, first derivative along x, y, z", "best": best,
                        "l2": "inputs larger than L2 (512^3 FP32 = 0.54 GB)"},
             "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s", "peak_kind": peak_kind,
-                         "tensor_peak_tflops": tf32_peak, "tensor_peak_kind": tf32_kind},
+                         "tensor_peak_tflops": tf32_peak, "tensor_peak_kind": tf32_kind,
+                         "bf16_peak_tflops": bf16_peak},
             "cases": rows}
     print(json.dumps(line))
     return 0

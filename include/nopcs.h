@@ -60,7 +60,9 @@ typedef enum {
     NOPCS_FORM_THOMAS = 1, /* per-sub-domain Thomas sweeps                      */
     NOPCS_FORM_GEMM_3XTF32 = 2, /* FP32 derivatives on the tensor cores (tcgen05, */
                                 /* split TF32); FP64 ones keep the Thomas form    */
-    NOPCS_FORM_GEMM_BF16X3 = 3, /* declared; returns NOPCS_EUNSUPPORTED          */
+    NOPCS_FORM_GEMM_BF16X3 = 3, /* FP32 derivatives on the tensor cores in three  */
+                                /* BF16 parts per operand (tcgen05 kind::f16, six */
+                                /* products); FP64 ones keep the Thomas form      */
     NOPCS_FORM_BANDED = 4  /* FP32 derivatives as the equivalent explicit scheme */
                            /* (Eq. CS:fpCf_i) at every row: rows of the global  */
                            /* C = A^-1 B truncated at 1e-8, no Thomas; FP64     */

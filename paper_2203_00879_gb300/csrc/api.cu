@@ -42,6 +42,7 @@ struct BoxRes {
     int sub_n[3] = {0, 0, 0};     // sub-domain length in use per axis (tuned if asked)
     int lines[3] = {0, 0, 0};     // flux-sweep lines per block per axis (0: default)
     bool deriv_gemm[3] = {false, false, false};  // FP32 derivative on the tensor cores
+    bool gemm_bf16[3] = {false, false, false};   // ... in the BF16x3 split (else 3xTF32)
     bool deriv_band[3] = {false, false, false};  // FP32 derivative in the banded explicit form
     BandBuf bop[3];                              // banded FP32 tables (forms BANDED and AUTO)
     bool mixed = false;
@@ -225,14 +226,15 @@ nopcs_status build_axis_ops(nopcs_ctx *ctx, BoxRes &b, int a)
             return fail(ctx, NOPCS_EUNSUPPORTED, "the banded form's tables do not fit its kernel for this line length");
         }
     }
-    if (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO) {
+    const bool gemm_form = ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_GEMM_BF16X3;
+    if (gemm_form || ctx->form == NOPCS_FORM_AUTO) {
         build_dense_blocks(b.dop32[a].host, b.gop[a].host);
         if (gemm_smem_fits(b.gop[a].host)) {
             CK(b.gop[a].upload(), "dense operator upload");
         } else {
             b.gop[a].release();
-            if (ctx->form == NOPCS_FORM_GEMM_3XTF32)
-                return fail(ctx, NOPCS_EUNSUPPORTED, "the tensor-core form needs sub-domains of at most 240 points");
+            if (gemm_form)
+                return fail(ctx, NOPCS_EUNSUPPORTED, "the tensor-core forms need sub-domains of at most 240 points");
         }
     }
     return NOPCS_OK;
@@ -334,6 +336,7 @@ nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
         CK(cudaMemsetAsync(fin, 0, 2 * (size_t)x.np * sizeof(float), st), "autotune");
         for (int a = 0; a < 3; ++a) {
             b.deriv_gemm[a] = false;
+            b.gemm_bf16[a] = false;
             b.deriv_band[a] = false;
             if (!b.gop[a].mem && !b.bop[a].mem) continue;
             const std::string key = std::string(key0) + ",g" + std::to_string(a) + "," + std::to_string(b.sub_n[a]);
@@ -344,20 +347,23 @@ nopcs_status autotune_box(nopcs_ctx *ctx, BoxRes &b)
                 if (it != g_tune_cache.end()) choice = it->second;
             }
             if (choice < 0) {
-                cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
-                const float tt = time_launches(st, [&] { return launch_line_field<float>(b.dop32[a].dev, a, x.n, fin, fout, 1.0, st); }, e1);
-                const float tg = b.gop[a].mem ? time_launches(st, [&] { return launch_gemm_field(b.gop[a].dev, a, x.n, fin, fout, 1.0, ctx->dev_err, st); }, e2) : 1e30f;
-                const float tb = b.bop[a].mem ? time_launches(st, [&] { return launch_band_field(b.bop[a], a, x.n, fin, fout, 1.0, st); }, e3) : 1e30f;
-                if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "autotune");
-                if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "autotune");
-                if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "autotune");
+                // 0 Thomas, 1 3xTF32, 2 banded, 3 BF16x3: the fastest
+                cudaError_t e[4] = {cudaSuccess, cudaSuccess, cudaSuccess, cudaSuccess};
+                float t[4];
+                t[0] = time_launches(st, [&] { return launch_line_field<float>(b.dop32[a].dev, a, x.n, fin, fout, 1.0, st); }, e[0]);
+                t[1] = b.gop[a].mem ? time_launches(st, [&] { return launch_gemm_field(b.gop[a].dev, false, a, x.n, fin, fout, 1.0, ctx->dev_err, st); }, e[1]) : 1e30f;
+                t[2] = b.bop[a].mem ? time_launches(st, [&] { return launch_band_field(b.bop[a], a, x.n, fin, fout, 1.0, st); }, e[2]) : 1e30f;
+                t[3] = b.gop[a].mem ? time_launches(st, [&] { return launch_gemm_field(b.gop[a].dev, true, a, x.n, fin, fout, 1.0, ctx->dev_err, st); }, e[3]) : 1e30f;
+                for (cudaError_t ei : e)
+                    if (ei != cudaSuccess) return cuda_fail(ctx, ei, "autotune");
                 choice = 0;
-                if (tg < tt && tg <= tb) choice = 1;
-                if (tb < tt && tb < tg) choice = 2;
+                for (int k = 1; k < 4; ++k)
+                    if (t[k] < t[choice]) choice = k;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 g_tune_cache[key] = choice;
             }
-            b.deriv_gemm[a] = choice == 1;
+            b.deriv_gemm[a] = choice == 1 || choice == 3;
+            b.gemm_bf16[a] = choice == 3;
             b.deriv_band[a] = choice == 2;
         }
     }
@@ -391,7 +397,8 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
 
     for (int a = 0; a < 3; ++a) {
         b.sub_n[a] = d.sub_n[a] == -1 ? 64 : d.sub_n[a];
-        b.deriv_gemm[a] = ctx->form == NOPCS_FORM_GEMM_3XTF32;
+        b.deriv_gemm[a] = ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_GEMM_BF16X3;
+        b.gemm_bf16[a] = ctx->form == NOPCS_FORM_GEMM_BF16X3;
         b.deriv_band[a] = ctx->form == NOPCS_FORM_BANDED;
         nopcs_status st = build_axis_ops(ctx, b, a);
         if (st != NOPCS_OK) return st;
@@ -718,8 +725,6 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
         std::string m;
         if (!valid_box(boxes[i], m)) return fail(nullptr, NOPCS_EINVAL, "box " + std::to_string(i) + ": " + m);
     }
-    if (form == NOPCS_FORM_GEMM_BF16X3)
-        return fail(nullptr, NOPCS_EUNSUPPORTED, "the BF16x3 tensor-core form is not built in this version");
     nopcs_ctx *ctx = new nopcs_ctx();
     ctx->prec = prec;
     ctx->form = form;
@@ -727,7 +732,8 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
     if (e == cudaSuccess) e = init_visc_kernels();
-    if (e == cudaSuccess && (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_AUTO))
+    if (e == cudaSuccess && (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_GEMM_BF16X3 ||
+                             ctx->form == NOPCS_FORM_AUTO))
         e = init_gemm_kernels();
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->dev_err, 0, sizeof(int));
@@ -855,8 +861,8 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
         }
         cudaError_t e;
         if (dtype == 1 && b.deriv_gemm[axis])
-            e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)f, (float *)b.scratch, scale,
-                                  ctx->dev_err, st);
+            e = launch_gemm_field(b.gop[axis].dev, b.gemm_bf16[axis], axis, b.dev.n, (const float *)f,
+                                  (float *)b.scratch, scale, ctx->dev_err, st);
         else if (dtype == 1 && b.deriv_band[axis])
             e = launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)f, (float *)b.scratch, scale, st);
         else if (dtype == 0)
@@ -868,7 +874,8 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
     }
     cudaError_t e;
     if (dtype == 1 && b.deriv_gemm[axis])
-        e = launch_gemm_field(b.gop[axis].dev, axis, b.dev.n, (const float *)src, (float *)df, scale, ctx->dev_err, st);
+        e = launch_gemm_field(b.gop[axis].dev, b.gemm_bf16[axis], axis, b.dev.n, (const float *)src, (float *)df,
+                              scale, ctx->dev_err, st);
     else if (dtype == 1 && b.deriv_band[axis])
         e = launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)src, (float *)df, scale, st);
     else if (dtype == 0)
@@ -993,7 +1000,7 @@ nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form
     for (int a = 0; a < 3; ++a) {
         if (sub_n) sub_n[a] = b.sub_n[a];
         if (deriv_form)
-            deriv_form[a] = b.deriv_gemm[a] ? NOPCS_FORM_GEMM_3XTF32
+            deriv_form[a] = b.deriv_gemm[a] ? (b.gemm_bf16[a] ? NOPCS_FORM_GEMM_BF16X3 : NOPCS_FORM_GEMM_3XTF32)
                                             : (b.deriv_band[a] ? NOPCS_FORM_BANDED : NOPCS_FORM_THOMAS);
         if (tile_lines) tile_lines[a] = b.lines[a];
     }

@@ -101,25 +101,32 @@ int partition_rule(int N, int sub_n, int *start);
 // FP64 host evaluation of a line operator (the arithmetic of the line kernels).
 void apply_line_host(const LineOpHost &op, const double *f, double *g);
 
-// Dense per-sub-domain operators for the tensor-core form.  Sub-domain b maps
+// Dense per-sub-domain operators for the tensor-core forms.  Sub-domain b maps
 // its staging window [tile_lo, tile_lo + Kpad) to its n_b outputs:
 // g = D_b f_window.  D_b is stored as B operands of tcgen05.mma (N = outputs,
-// K = window), K-major, no swizzle, split into TF32 hi and lo parts:
-// element (n, k) of a block sits at float offset
-//   (n / 8) * (Kpad / 4) * 32 + (k / 4) * 32 + (n % 8) * 4 + (k % 4).
+// K = window), K-major, no swizzle, in two splits:
+//   - TF32 hi and lo parts (3xTF32 form); element (n, k) of a block sits at
+//     float offset (n / 8) * (Kpad / 4) * 32 + (k / 4) * 32 + (n % 8) * 4 + (k % 4);
+//   - three BF16 parts, D = D1 + D2 + D3 (BF16x3 form), the window padded to
+//     Kpad16 (a multiple of 16, the K of one kind::f16 MMA); element (n, k) at
+//     16-bit offset (n / 8) * (Kpad16 / 8) * 64 + (k / 8) * 64 + (n % 8) * 8 + (k % 8).
 struct DenseHost {
-    int N = 0, nsub = 0, max_npad = 0, max_kpad = 0;
-    std::vector<int> rec;       // per sub-domain: s, n_b, Npad, Kpad, window start, float offset
-    std::vector<float> hi, lo;  // concatenated blocks
+    int N = 0, nsub = 0, max_npad = 0, max_kpad = 0, max_kpad16 = 0;
+    // per sub-domain: s, n_b, Npad, Kpad, window start, float offset, Kpad16,
+    // 16-bit offset
+    std::vector<int> rec;
+    std::vector<float> hi, lo;            // concatenated TF32 parts
+    std::vector<uint16_t> b16[3];         // concatenated BF16 parts (bit patterns)
 };
-constexpr int DENSE_REC = 6;
+constexpr int DENSE_REC = 8;
 void build_dense_blocks(const LineOpHost &op, DenseHost &out);
 
 // Device view of the dense blocks (tensor-core form).
 struct GemmOpDev {
-    int N, nsub, max_npad, max_kpad;
+    int N, nsub, max_npad, max_kpad, max_kpad16;
     const int *rec;
     const float *hi, *lo;
+    const uint16_t *b16[3];
 };
 struct GemmOpBuf {
     DenseHost host;
@@ -130,9 +137,9 @@ struct GemmOpBuf {
 };
 cudaError_t init_gemm_kernels();
 bool gemm_smem_fits(const DenseHost &h);
-// FP32 field derivative by the 3xTF32 tensor-core form; err <- 1 if a bounded
-// wait for the tensor cores gave up.
-cudaError_t launch_gemm_field(const GemmOpDev &op, int axis, const int n[3], const float *f, float *out,
+// FP32 field derivative by a tensor-core form, 3xTF32 (bf16x3 false) or BF16x3
+// (true); err <- 1 if a bounded wait for the tensor cores gave up.
+cudaError_t launch_gemm_field(const GemmOpDev &op, bool bf16x3, int axis, const int n[3], const float *f, float *out,
                               double scale, int *err, cudaStream_t st);
 
 // Owns the device copy of a LineOpHost.

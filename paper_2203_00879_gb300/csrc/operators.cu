@@ -415,11 +415,23 @@ void build_dense_blocks(const LineOpHost &op, DenseHost &out)
         memcpy(&y, &u, 4);
         return y;
     };
+    // nearest BF16 value (ties to even): its bit pattern and its value
+    auto bf16 = [](double x, uint16_t &bits) {
+        const float xf = (float)x;
+        unsigned u;
+        memcpy(&u, &xf, 4);
+        u += 0x7FFFu + ((u >> 16) & 1u);
+        bits = (uint16_t)(u >> 16);
+        const unsigned v = (unsigned)bits << 16;
+        float y;
+        memcpy(&y, &v, 4);
+        return (double)y;
+    };
     for (int b = 0; b < op.nsub; ++b) {
         const int *rec = &op.sub[(size_t)b * SUB_REC];
         const int s = rec[0], e = rec[1], tlo = rec[2], thi = rec[3];
         const int nb = e - s + 1, K = thi - tlo + 1;
-        const int npad = (nb + 15) / 16 * 16, kpad = (K + 7) / 8 * 8;
+        const int npad = (nb + 15) / 16 * 16, kpad = (K + 7) / 8 * 8, kpad16 = (K + 15) / 16 * 16;
         int *r = &out.rec[(size_t)b * DENSE_REC];
         r[0] = s;
         r[1] = nb;
@@ -427,11 +439,15 @@ void build_dense_blocks(const LineOpHost &op, DenseHost &out)
         r[3] = kpad;
         r[4] = tlo;
         r[5] = (int)out.hi.size();
+        r[6] = kpad16;
+        r[7] = (int)out.b16[0].size();
         out.max_npad = npad > out.max_npad ? npad : out.max_npad;
         out.max_kpad = kpad > out.max_kpad ? kpad : out.max_kpad;
-        const size_t base = out.hi.size();
+        out.max_kpad16 = kpad16 > out.max_kpad16 ? kpad16 : out.max_kpad16;
+        const size_t base = out.hi.size(), base16 = out.b16[0].size();
         out.hi.resize(base + (size_t)npad * kpad, 0.0f);
         out.lo.resize(base + (size_t)npad * kpad, 0.0f);
+        for (auto &v : out.b16) v.resize(base16 + (size_t)npad * kpad16, 0);
         for (int k = 0; k < K; ++k) {
             std::fill(f.begin(), f.end(), 0.0);
             f[tlo + k] = 1.0;
@@ -443,6 +459,11 @@ void build_dense_blocks(const LineOpHost &op, DenseHost &out)
                 const size_t o = base + (size_t)(n / 8) * (kpad / 4) * 32 + (size_t)(k / 4) * 32 + (n % 8) * 4 + (k % 4);
                 out.hi[o] = h;
                 out.lo[o] = l;
+                // three BF16 parts, each of what the earlier ones leave
+                const size_t o16 =
+                    base16 + (size_t)(n / 8) * (kpad16 / 8) * 64 + (size_t)(k / 8) * 64 + (n % 8) * 8 + (k % 8);
+                double rest = d;
+                for (int q = 0; q < 3; ++q) rest -= bf16(rest, out.b16[q][o16]);
             }
         }
     }

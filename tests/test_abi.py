@@ -55,9 +55,13 @@ def test_init_rejects_bad_arguments_before_device_work(N):
         assert ei.value.status == N.NOPCS_EINVAL
     with pytest.raises(N.NopcsError):
         N.nopcs_init([good], prec=7)
+    for form in (-1, N.NOPCS_FORM_BANDED + 1):
+        with pytest.raises(N.NopcsError) as ei:
+            N.nopcs_init([good], form=form)
+        assert ei.value.status == N.NOPCS_EINVAL
     with pytest.raises(N.NopcsError) as ei:
-        N.nopcs_init([good], form=N.NOPCS_FORM_GEMM_BF16X3)
-    assert ei.value.status == N.NOPCS_EUNSUPPORTED
+        N.nopcs_init([dict(good, visc_compact=2)])
+    assert ei.value.status == N.NOPCS_EINVAL
 
 
 def test_kernel_names(N):

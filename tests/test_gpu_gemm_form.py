@@ -1,5 +1,6 @@
-"""Parity of the tensor-core (3xTF32 tcgen05) form of nopcs_derivative with the
-FP64 oracle: FP32 fields, <= 1e-5 of max |f'| (order 1), 5e-5 (order 2)."""
+"""Parity of the tensor-core forms of nopcs_derivative (tcgen05: 3xTF32, and
+BF16x3 with three BF16 parts per operand) with the FP64 oracle: FP32 fields,
+<= 1e-5 of max |f'| (order 1), 5e-5 (order 2)."""
 import numpy as np
 import pytest
 
@@ -10,17 +11,22 @@ from gpu_util import binding, field_rel, stream_ptr, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _ctx(N, n, sub_n):
+FORMS = ("3xtf32", "bf16x3")
+
+
+def _ctx(N, n, sub_n, form="3xtf32"):
     p = S.box_params(n, sub_n=sub_n, perturb_amp=0.0)
-    return N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_GEMM_3XTF32, stream=stream_ptr()), p
+    f = N.NOPCS_FORM_GEMM_3XTF32 if form == "3xtf32" else N.NOPCS_FORM_GEMM_BF16X3
+    return N.nopcs_init([p], prec=N.NOPCS_MIXED, form=f, stream=stream_ptr()), p
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n,sub_n", [((40, 36, 33), (16, 16, 16)), ((130, 66, 35), (64, 32, 8)),
                                      ((200, 140, 129), (64, 64, 64)), ((7, 9, 11), (3, 4, 5))])
-def test_gemm_form_parity(n, sub_n):
+def test_gemm_form_parity(n, sub_n, form):
     import torch
     N = binding()
-    ctx, p = _ctx(N, n, sub_n)
+    ctx, p = _ctx(N, n, sub_n, form)
     try:
         f = S.sine_field(n, kmax=16, seed=7, noise=1e-3)
         fd = to_dev(f, np.float32)
@@ -37,19 +43,20 @@ def test_gemm_form_parity(n, sub_n):
                 if order == 2:
                     ref = oracle.deriv3d(ref, axis, h, sub_n[axis])
                 err = field_rel(got[None], ref[None])[0]
-                print("gemm parity", n, sub_n, "axis", axis, "order", order, "err %.3e" % err)
+                print("gemm parity", form, n, sub_n, "axis", axis, "order", order, "err %.3e" % err)
                 assert np.all(np.isfinite(got)), (axis, order)
                 assert err <= (1e-5 if order == 1 else 5e-5), (axis, order, err)
     finally:
         N.nopcs_destroy(ctx)
 
 
-def test_gemm_form_fp64_fields_use_thomas():
+@pytest.mark.parametrize("form", FORMS)
+def test_gemm_form_fp64_fields_use_thomas(form):
     """FP64 fields keep the Thomas form under a tensor-core context (<= 1e-12)."""
     import torch
     N = binding()
     n = (40, 36, 33)
-    ctx, p = _ctx(N, n, (16, 16, 16))
+    ctx, p = _ctx(N, n, (16, 16, 16), form)
     try:
         f = S.sine_field(n, kmax=8, seed=3, noise=0.0)
         fd = to_dev(f)
@@ -74,8 +81,8 @@ def test_autotuner_choices_and_parity():
     try:
         info = N.nopcs_box_info(ctx, 0)
         assert all(sn in (32, 64, 128) for sn in info["sub_n"]), info
-        assert all(fm in (N.NOPCS_FORM_THOMAS, N.NOPCS_FORM_GEMM_3XTF32, N.NOPCS_FORM_BANDED)
-                   for fm in info["deriv_form"]), info
+        assert all(fm in (N.NOPCS_FORM_THOMAS, N.NOPCS_FORM_GEMM_3XTF32, N.NOPCS_FORM_GEMM_BF16X3,
+                          N.NOPCS_FORM_BANDED) for fm in info["deriv_form"]), info
         f = S.sine_field(n, kmax=16, seed=5, noise=1e-3)
         fd = to_dev(f, np.float32)
         out = torch.empty_like(fd)
@@ -96,3 +103,28 @@ def test_autotuner_choices_and_parity():
         assert np.all(field_rel(Q.cpu().numpy(), ref) <= 1e-5)
     finally:
         N.nopcs_destroy(ctx)
+
+
+def test_bf16x3_reports_its_form_and_matches_3xtf32_on_a_512_line():
+    """A full-length 512-point line tile (the microbenchmark's line length):
+    both tensor-core forms agree with the oracle on sampled lines."""
+    import torch
+    N = binding()
+    n = (512, 16, 16)
+    out = {}
+    for form in FORMS:
+        ctx, p = _ctx(N, n, (64, 16, 16), form)
+        try:
+            info = N.nopcs_box_info(ctx, 0)
+            want = N.NOPCS_FORM_GEMM_3XTF32 if form == "3xtf32" else N.NOPCS_FORM_GEMM_BF16X3
+            assert all(fm == want for fm in info["deriv_form"]), info
+            f = S.sine_field(n, kmax=64, seed=9, noise=1e-3)
+            fd = to_dev(f, np.float32)
+            o = torch.empty_like(fd)
+            N.nopcs_derivative(ctx, 0, 0, 1, 1, fd.data_ptr(), o.data_ptr(), stream_ptr())
+            N.nopcs_synchronize(ctx)
+            out[form] = o.cpu().numpy().astype(np.float64)
+            ref = oracle.deriv3d(fd.cpu().numpy().astype(np.float64), 0, p["len"][0] / 511, 64)
+            assert field_rel(out[form][None], ref[None])[0] <= 1e-5
+        finally:
+            N.nopcs_destroy(ctx)

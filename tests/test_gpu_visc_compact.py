@@ -166,3 +166,33 @@ def test_compact_and_explicit_boxes_in_one_context():
             assert np.array_equal(_state(N, c1, p), both[b])
         finally:
             N.nopcs_destroy(c1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,sub_n", [((5, 5, 5), (0, 0, 0)), ((5, 7, 6), (3, 3, 3)), ((9, 5, 11), (3, 0, 4))])
+def test_compact_viscous_smallest_boxes(prec, n, sub_n):
+    """The smallest boxes (5 points per axis) and sub-domains (3 points):
+    every line is almost all wall-closure rows and sub-domain ends."""
+    import torch
+    N = binding()
+    p = S.box_params(n, sub_n=sub_n, base_subtract=1, perturb_amp=1e-3, seed=6, Re=20.0, visc_compact=1)
+    ctx = N.nopcs_init([p], prec=prec, stream=stream_ptr())
+    try:
+        orc = oracle.Solver(p)
+        Q = _perturbed(orc, 2)
+        ref = _no_slip(orc.rhs(Q))
+        r = torch.empty(Q.shape, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+        N.nopcs_rhs(ctx, 0, to_dev(Q).data_ptr(), r.data_ptr())
+        got = r.cpu().numpy().astype(np.float64)
+        d = np.abs(got - ref).reshape(5, -1).max(axis=1)
+        s_ = np.abs(ref).reshape(5, -1).max(axis=1)
+        if prec == 0:
+            pr = (p["gamma"] - 1) * (Q[4] - 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0])
+            h = p["len"][0] / (p["n"][0] - 1)
+            floor = 30 * np.finfo(float).eps * np.abs(pr).max() / h
+            gate = 1e-12 * s_ + np.r_[0.0, floor, floor, floor, 0.0]
+        else:
+            gate = 1e-4 * s_
+        assert np.all(d <= gate), (d / s_, gate / s_)
+    finally:
+        N.nopcs_destroy(ctx)

@@ -168,14 +168,17 @@ def test_compact_and_explicit_boxes_in_one_context():
             N.nopcs_destroy(c1)
 
 
+@pytest.mark.parametrize("visc_compact", [1, 0])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n,sub_n", [((5, 5, 5), (0, 0, 0)), ((5, 7, 6), (3, 3, 3)), ((9, 5, 11), (3, 0, 4))])
-def test_compact_viscous_smallest_boxes(prec, n, sub_n):
-    """The smallest boxes (5 points per axis) and sub-domains (3 points):
-    every line is almost all wall-closure rows and sub-domain ends."""
+def test_smallest_boxes(prec, n, sub_n, visc_compact):
+    """The smallest boxes (5 points per axis) and sub-domains (3 points),
+    with compact and with the paper's explicit viscous terms: every line is
+    almost all wall-closure rows and sub-domain ends, and the explicit
+    viscous kernel's 32 x 8 tile is wider than the box."""
     import torch
     N = binding()
-    p = S.box_params(n, sub_n=sub_n, base_subtract=1, perturb_amp=1e-3, seed=6, Re=20.0, visc_compact=1)
+    p = S.box_params(n, sub_n=sub_n, base_subtract=1, perturb_amp=1e-3, seed=6, Re=20.0, visc_compact=visc_compact)
     ctx = N.nopcs_init([p], prec=prec, stream=stream_ptr())
     try:
         orc = oracle.Solver(p)

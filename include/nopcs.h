@@ -247,8 +247,9 @@ nopcs_status nopcs_plane_fields(nopcs_ctx *ctx, int box, int axis, int index, in
  * Choices in force for box `box` (caller arrays of 3 ints, any may be NULL):
  * the sub-domain length per axis (the autotuner's pick where the descriptor
  * asked for -1), the form of the FP32 derivative per axis (NOPCS_FORM_THOMAS,
- * NOPCS_FORM_GEMM_3XTF32 or NOPCS_FORM_BANDED) and the flux sweeps' tile width per axis (grid
- * lines per CUDA block; 0 = the precision's default, untuned for small boxes).
+ * NOPCS_FORM_GEMM_3XTF32, NOPCS_FORM_GEMM_BF16X3 or NOPCS_FORM_BANDED) and the
+ * flux sweeps' tile width per axis (grid lines per CUDA block; 0 = the
+ * precision's default, untuned for small boxes).
  */
 nopcs_status nopcs_box_info(nopcs_ctx *ctx, int box, int *sub_n, int *deriv_form, int *tile_lines);
 

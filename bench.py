@@ -466,16 +466,22 @@ def main():
             p64 = box(n64, args.sub_n, seed=1 + rank)
             ctx = N.nopcs_init([p64], prec=N.NOPCS_FP64, stream=st)
         N.nopcs_rk_step(ctx, 1)
+        N.nopcs_set_profiling(ctx, True)
+        N.nopcs_profile_read(ctx, reset=True)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        profiler_range(True)
         e0.record(stream)
         N.nopcs_rk_step(ctx, args.fp64_steps)
         e1.record(stream)
+        profiler_range(False)
         barrier()
         m64 = rank_max(e0.elapsed_time(e1))
+        p64k = N.nopcs_profile_read(ctx, reset=True)
         v64 = world * float(n64) ** 3 * 4 * args.fp64_steps / (m64 * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "grid": [n64] * 3, "steps": args.fp64_steps,
-                "ms_per_step": m64 / args.fp64_steps, "mixed_over_fp64": value / v64}
+                "ms_per_step": m64 / args.fp64_steps, "mixed_over_fp64": value / v64,
+                "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in p64k.items() if v[1]}}
         N.nopcs_destroy(ctx)
 
     # mixed form with compact viscous terms (NOHAP gradients and divergence)

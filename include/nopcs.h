@@ -45,7 +45,7 @@ typedef enum {
     NOPCS_ECUDA = 3,       /* a CUDA call failed; the context should be destroyed */
     NOPCS_EUNSTABLE = 4,   /* non-finite values found in the state              */
     NOPCS_ETIMEOUT = 5,    /* a bounded device wait gave up                     */
-    NOPCS_EUNSUPPORTED = 6 /* valid request this build does not implement       */
+    NOPCS_EUNSUPPORTED = 6 /* valid request that is not implemented             */
 } nopcs_status;
 
 typedef enum {

@@ -80,9 +80,9 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 
 // Ask L2 for what the RK update of node p will load: its right-hand side and
 // (mixed form) K, D_n and, in stage 4, Q_n.  Issued a plane ahead, these take
-// the DRAM latency off the update, which runs after the plane's barrier with
-// no registers to spare for loading early (the 64-register cap keeps four
-// blocks per SM).
+// the DRAM latency off the update, which runs after the plane's barrier; an L2
+// prefetch holds no register (loading them into registers before the flux
+// phase instead was slower).
 template <typename T>
 __device__ __forceinline__ void prefetch_node(const VArgs<T> &a, int p)
 {
@@ -608,10 +608,11 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     }
 }
 
-// FP32: at most 64 registers, which with 56 KB of shared memory per block
-// keeps four blocks (32 warps) on an SM
+// FP32: three blocks (24 warps) per SM, with up to 85 registers per thread
+// (the kernel takes 78); a 64-register cap for four blocks was 1.4% slower
+// once the L2 prefetches had taken the load latency off the update
 template <typename T>
-__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 1024 : 512) / (TX * TY)) visc_rk_kernel(const VArgs<T> a)
+__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) visc_rk_kernel(const VArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     // blocks whose x and y ranges (with the one-node flux halo) stay off the

@@ -74,6 +74,7 @@ def lib():
         L.orc_initial_state.argtypes = [C.c_void_p, _dp]
         L.orc_rhs.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_apply_wall_bc.argtypes = [C.c_void_p, _dp]
+        L.orc_set_wall_extrapolation.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_filter.argtypes = [C.c_void_p, _dp]
         L.orc_rk_steps.argtypes = [C.c_void_p, _dp, C.c_int]
         L.orc_solver_step.argtypes = [C.c_void_p]
@@ -215,6 +216,12 @@ class Solver:
         Q = np.array(Q, dtype=np.float64, order="C")
         lib().orc_apply_wall_bc(self._s, Q)
         return Q
+
+    @staticmethod
+    def set_wall_extrapolation(w1: float = 4.0, w2: float = 1.0, w3: float = 3.0):
+        """Weights of T_w = (w1 T_1 - w2 T_2) / w3 for every solver (default: the
+        adiabatic rule).  For tests that plant a wrong rule; restore afterwards."""
+        lib().orc_set_wall_extrapolation(float(w1), float(w2), float(w3))
 
     def filter(self, Q):
         Q = np.array(Q, dtype=np.float64, order="C")

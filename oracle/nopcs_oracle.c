@@ -40,9 +40,12 @@
  *     temperature T_w = (4 T_1 - T_2)/3, applied face -> edge -> corner;
  *   - Sutherland constant S = 110.4 K, bulk viscosity mu_b / mu_s with mu_s the
  *     dimensional viscosity at T_s, heat flux exactly as Eq. ge20.
- * Parity unpinned: the wall boundary-condition hierarchy (orc_apply_wall_bc) and
- * the corner/edge averaging in it have no pin in the paper or in a closed form;
- * the tests only check invariants (symmetry, rest state, conservation).
+ * The wall conditions (orc_apply_wall_bc) are pinned by closed forms: a
+ * temperature T0 + a (x - x_w)^2 + b (y - y_w)^2 + c (z - z_w)^2, whose normal
+ * gradient vanishes on the walls x = x_w, y = y_w, z = z_w, must come back
+ * exactly on every face, edge and corner node of those walls (the extrapolation
+ * is exact for quadratics with zero slope at the wall), with zero momentum,
+ * unchanged density and E_w = rho_w T_w / (gamma (gamma - 1) M^2).
  */
 #include <math.h>
 #include <stdint.h>
@@ -702,6 +705,22 @@ static double temp_at(const orc_box *bx, const double *Q, long long np, long lon
 }
 
 /*
+ * Weights of the one-sided wall-temperature extrapolation,
+ * T_w = (w1 T_1 - w2 T_2) / w3.  The defaults (4, 1, 3) make the one-sided
+ * second-order normal difference (-3 T_w + 4 T_1 - T_2) / (2h) vanish, which
+ * is the adiabatic wall of Sec. 2 (Fig. 1) to second order.  The setter exists
+ * only so that a test can plant a wrong rule and see its closed-form pin fail.
+ */
+static double g_wall_w[3] = {4.0, 1.0, 3.0};
+
+void orc_set_wall_extrapolation(double w1, double w2, double w3)
+{
+    g_wall_w[0] = w1;
+    g_wall_w[1] = w2;
+    g_wall_w[2] = w3;
+}
+
+/*
  * No-slip adiabatic walls (reading): momentum is zero on every wall node; the
  * wall temperature is T_w = (4 T_1 - T_2)/3 along the inward normal (zero
  * normal gradient to 2nd order), averaged over the normals of edge and corner
@@ -723,7 +742,8 @@ void orc_apply_wall_bc(const orc_solver *s, double *Q)
             double Tw = 0.0;
             for (int t = 0; t < nw; ++t) {
                 long long st = sg[t] * stride[dirs[t]];
-                Tw += (4.0 * temp_at(bx, Q, np, p + st) - temp_at(bx, Q, np, p + 2 * st)) / 3.0;
+                Tw += (g_wall_w[0] * temp_at(bx, Q, np, p + st) - g_wall_w[1] * temp_at(bx, Q, np, p + 2 * st)) /
+                      g_wall_w[2];
             }
             Tw /= nw;
             Q[4 * np + p] = Q[p] * Tw * cE;

@@ -356,3 +356,100 @@ def test_wall_bc_properties():
     # interior untouched, density untouched
     assert np.array_equal(Qb[:, 1:-1, 1:-1, 1:-1], Q[:, 1:-1, 1:-1, 1:-1])
     assert np.array_equal(Qb[0], Q[0])
+
+
+def _quadratic_wall_state(p, walls, T0=1.3, coef=(0.7, -0.4, 0.9), seed=5):
+    """A state whose temperature is T0 + sum_d c_d (x_d - w_d)^2, with w_d the
+    coordinate of the chosen wall along axis d (0 or len_d), so the normal
+    gradient of T vanishes on those three walls.  Density and the interior
+    velocity are random; wall nodes start with a wrong temperature and a
+    nonzero velocity."""
+    n, L = p["n"], p["len"]
+    gam, M = p["gamma"], p["M"]
+    cE = 1.0 / (gam * (gam - 1) * M * M)
+    x = [np.arange(n[d]) * (L[d] / (n[d] - 1)) for d in range(3)]
+    Z, Y, X = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    T = T0 + coef[0] * (X - walls[0]) ** 2 + coef[1] * (Y - walls[1]) ** 2 + coef[2] * (Z - walls[2]) ** 2
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.3 * rng.uniform(size=T.shape)
+    V = rng.uniform(-0.2, 0.2, size=(3,) + T.shape)
+    Tstart = T * (1.0 + 0.05 * rng.standard_normal(T.shape))  # the wall nodes must not keep this
+    interior = np.zeros(T.shape, dtype=bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    Tstart = np.where(interior, T, Tstart)
+    Q = np.empty((5,) + T.shape)
+    Q[0] = rho
+    Q[1:4] = rho * V
+    Q[4] = rho * Tstart * cE + 0.5 * rho * (V ** 2).sum(0)
+    return Q, T
+
+
+def _wall_mask(p, walls):
+    """Wall nodes all of whose walls are among the chosen ones (x = walls[0],
+    y = walls[1], z = walls[2])."""
+    n, L = p["n"], p["len"]
+    idx = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")[::-1]
+    on_any = np.zeros(idx[0].shape, dtype=bool)
+    on_other = np.zeros(idx[0].shape, dtype=bool)
+    for d in range(3):
+        chosen = 0 if walls[d] == 0.0 else n[d] - 1
+        other = n[d] - 1 - chosen
+        on_any |= (idx[d] == chosen) | (idx[d] == other)
+        on_other |= idx[d] == other
+    return on_any & ~on_other
+
+
+def _check_quadratic_walls(s, p, walls):
+    Q, Tex = _quadratic_wall_state(p, walls)
+    Qb = s.wall_bc(Q)
+    gam, M = p["gamma"], p["M"]
+    ke = 0.5 * (Qb[1] ** 2 + Qb[2] ** 2 + Qb[3] ** 2) / Qb[0]
+    T = gam * (gam - 1) * M * M * (Qb[4] - ke) / Qb[0]
+    m = _wall_mask(p, walls)
+    return Q, Qb, T, Tex, m
+
+
+def test_wall_bc_exact_for_quadratic_adiabatic_temperature():
+    """Closed-form pin of the adiabatic no-slip walls (Sec. 2, Fig. 1): for
+    T = T0 + a (x - x_w)^2 + b (y - y_w)^2 + c (z - z_w)^2 the normal gradient
+    is zero on x = x_w, y = y_w and z = z_w, and the rule T_w = (4 T_1 - T_2)/3
+    must return the analytic wall temperature on every face, edge and corner
+    node of those walls, for all eight choices of the three walls."""
+    p = S.box_params((9, 10, 11), perturb_amp=0.0)
+    p["len"] = (1.0, 1.3, 0.8)
+    s = oracle.Solver(p)
+    gam, M = p["gamma"], p["M"]
+    cE = 1.0 / (gam * (gam - 1) * M * M)
+    for wx in (0.0, p["len"][0]):
+        for wy in (0.0, p["len"][1]):
+            for wz in (0.0, p["len"][2]):
+                walls = (wx, wy, wz)
+                Q, Qb, T, Tex, m = _check_quadratic_walls(s, p, walls)
+                nfaces = m.sum()
+                assert nfaces > 0
+                err = np.max(np.abs(T[m] - Tex[m]) / Tex[m])
+                assert err < 1e-13, (walls, err)
+                # E_w = rho_w T_w / (gamma (gamma - 1) M^2) with zero momentum
+                assert np.allclose(Qb[4][m], Qb[0][m] * Tex[m] * cE, rtol=1e-13, atol=0)
+                for c in (1, 2, 3):
+                    assert np.all(Qb[c][m] == 0.0)
+                assert np.array_equal(Qb[0], Q[0])  # density keeps its continuity value
+                assert np.array_equal(Qb[:, 1:-1, 1:-1, 1:-1], Q[:, 1:-1, 1:-1, 1:-1])
+
+
+def test_wall_bc_closed_form_rejects_planted_extrapolation():
+    """Planting the first-order-accurate (3 T_1 - T_2)/2 (zero slope only to
+    first order) or a wrong normal weight in the oracle must fail the
+    closed-form pin above."""
+    p = S.box_params((9, 10, 11), perturb_amp=0.0)
+    s = oracle.Solver(p)
+    try:
+        for w in ((3.0, 1.0, 2.0), (4.0, 1.0, 3.0 + 1e-9), (1.0, 0.0, 1.0)):
+            oracle.Solver.set_wall_extrapolation(*w)
+            Q, Qb, T, Tex, m = _check_quadratic_walls(s, p, (0.0, 0.0, 0.0))
+            err = np.max(np.abs(T[m] - Tex[m]) / Tex[m])
+            assert err > 1e-10, (w, err)
+    finally:
+        oracle.Solver.set_wall_extrapolation()
+    Q, Qb, T, Tex, m = _check_quadratic_walls(s, p, (0.0, 0.0, 0.0))
+    assert np.max(np.abs(T[m] - Tex[m]) / Tex[m]) < 1e-13

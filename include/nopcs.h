@@ -27,7 +27,15 @@
  *     The library owns the state registers, scratch, operator tables and CUDA
  *     graphs of a context and frees them in nopcs_destroy().
  *   - Streams are cudaStream_t values passed as void* (NULL = legacy default).
- *   - The library runs on the CUDA device current at nopcs_init().
+ *   - The library runs on the CUDA device current at nopcs_init().  Every
+ *     later call on the context must be made with that device current, else
+ *     it returns NOPCS_EINVAL and enqueues nothing; nopcs_destroy() switches
+ *     to the context's device itself and switches back.
+ *   - Device memory: nopcs_init allocates a context's registers, scratch and
+ *     tables; nopcs_derivative(order = 2) allocates its scratch on first use.
+ *     An allocation that fails, or that would take the context beyond the
+ *     limit of nopcs_set_memory_limit, is NOPCS_ENOMEM, and a failed
+ *     nopcs_init frees everything it had allocated.
  */
 #ifndef NOPCS_H
 #define NOPCS_H
@@ -136,6 +144,16 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
 /* Free everything the context owns (waits for its stream).  NULL is a no-op. */
 void nopcs_destroy(nopcs_ctx *ctx);
 
+/*
+ * Cap, in bytes, on the device memory that each context created afterwards
+ * may hold (its state registers, scratch and operator tables); 0 (the
+ * default) removes the cap.  Process-wide.  A nopcs_init that would exceed it
+ * returns NOPCS_ENOMEM with nothing left allocated; so does a later order-2
+ * nopcs_derivative whose scratch would exceed it.  The paper has no
+ * counterpart: this serves callers with a fixed memory budget per job.
+ */
+nopcs_status nopcs_set_memory_limit(unsigned long long bytes);
+
 /* Message of the last failed call on this context (or of the last failed
  * nopcs_init when ctx is NULL); never NULL. */
 const char *nopcs_last_error(const nopcs_ctx *ctx);
@@ -150,6 +168,15 @@ nopcs_status nopcs_get_state(nopcs_ctx *ctx, int box, double *q);
 
 /* Reset box `box` to its initial state and its step counter to 0. */
 nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box);
+
+/*
+ * Set box `box`'s RK step counter (the count the filter cadence of Sec. 4,
+ * every filter_every steps, is taken from), e.g. to resume from a checkpoint
+ * written with nopcs_get_state and the `step` of nopcs_diagnostics: after
+ * nopcs_set_state and nopcs_set_step the box continues exactly as the run
+ * that wrote the checkpoint.  Errors: EINVAL (step < 0, bad box).
+ */
+nopcs_status nopcs_set_step(nopcs_ctx *ctx, int box, long long step);
 
 /*
  * NOHAP compact derivative of one field of box `box`'s shape along `axis`
@@ -178,14 +205,16 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
  * own pool allocator, or the implicit synchronisation of cudaMalloc/cudaFree
  * is not acceptable in their loop), whereas nopcs_derivative allocates its
  * order-2 scratch on first use.  Same arguments, result and arithmetic as
- * nopcs_derivative with order 2; the intermediate first derivative lives in a
- * fixed 16 MiB array in the library's device image, which every GPU that loads
- * the library holds until the process exits.  Limits and behaviour:
+ * nopcs_derivative with order 2, including the form of each axis's FP32
+ * derivative (Thomas, banded or tensor-core, as chosen at nopcs_init), so the
+ * two give identical bits; the intermediate first derivative lives in a fixed
+ * 16 MiB array in the library's device image.  Limits and behaviour:
+ *   - the array becomes resident on a device when the first context is
+ *     created there (nopcs_init looks up its device address, with that
+ *     device current) and stays until the process exits; no call of this
+ *     entry point loads a module or looks the address up again;
  *   - fields of at most 2^21 FP64 or 2^22 FP32 points; larger ones return
  *     NOPCS_EINVAL with a message (nothing is enqueued);
- *   - the first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture;
  *   - all calls share the one array, so two calls whose work overlaps on the
  *     GPU (different streams, no ordering between them) race on it; the array
  *     keeps the last call's contents, and each call overwrites every element

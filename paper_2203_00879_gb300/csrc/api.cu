@@ -4,10 +4,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <functional>
 #include <map>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "nopcs_internal.cuh"
@@ -23,6 +25,26 @@ const char *const KERNEL_NAMES[NOPCS_NUM_KERNELS] = {
 enum { K_PREP = 0, K_SX, K_SY, K_SZ, K_VISC, K_BC, K_FILTER, K_DIAG, K_VGRAD, K_VFLUX, K_VDIV, K_SRC };
 
 thread_local std::string g_init_error;
+
+// ---- device memory accounting -------------------------------------------------
+// nopcs_set_memory_limit caps the device bytes one context may hold (0: no
+// cap).  Each context keeps a ledger of its allocations; while one of its
+// entry points runs, t_ledger points to it and dev_alloc / dev_free book
+// there.  Allocations outside an entry point (none today) are not counted.
+std::atomic<unsigned long long> g_mem_limit{0};
+
+struct Ledger {
+    unsigned long long limit = 0, used = 0;
+    std::unordered_map<void *, size_t> sizes;
+};
+thread_local Ledger *t_ledger = nullptr;
+
+// books the context's ledger for the duration of an entry point
+struct LedgerScope {
+    Ledger *prev;
+    explicit LedgerScope(Ledger *l) : prev(t_ledger) { t_ledger = l; }
+    ~LedgerScope() { t_ledger = prev; }
+};
 
 // Device registers of a box.
 //   FP64 form: Q = Qn, Qs, acc (15 FP64 fields); W (6 FP64); R (5 FP64).
@@ -72,6 +94,7 @@ struct ProfPair {
 
 struct nopcs_ctx {
     int device = 0;
+    Ledger ledger;
     nopcs_precision prec = NOPCS_FP64;
     nopcs_form form = NOPCS_FORM_THOMAS;
     cudaStream_t stream = nullptr;
@@ -100,9 +123,12 @@ nopcs_status fail(nopcs_ctx *c, nopcs_status s, const std::string &m)
     return s;
 }
 
+// an allocation that failed (the device is full, or the context's memory
+// limit is reached) is NOPCS_ENOMEM; every other CUDA error NOPCS_ECUDA
 nopcs_status cuda_fail(nopcs_ctx *c, cudaError_t e, const char *what)
 {
-    return fail(c, NOPCS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return fail(c, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 #define CK(call, what)                                   \
@@ -182,15 +208,15 @@ void free_box(BoxRes &b)
         b.gop[a].release();
         b.bop[a].release();
     }
-    if (b.Q) cudaFree(b.Q);
-    if (b.W) cudaFree(b.W);
-    if (b.R) cudaFree(b.R);
-    if (b.Gv) cudaFree(b.Gv);
-    if (b.base) cudaFree(b.base);
-    if (b.partial) cudaFree(b.partial);
-    if (b.scratch) cudaFree(b.scratch);
+    if (b.Q) dev_free(b.Q);
+    if (b.W) dev_free(b.W);
+    if (b.R) dev_free(b.R);
+    if (b.Gv) dev_free(b.Gv);
+    if (b.base) dev_free(b.base);
+    if (b.partial) dev_free(b.partial);
+    if (b.scratch) dev_free(b.scratch);
     b.Q = nullptr;
-    b.W = b.R = b.base = b.scratch = nullptr;
+    b.W = b.R = b.Gv = b.base = b.scratch = nullptr;
     b.partial = b.diag_out = nullptr;
 }
 
@@ -431,7 +457,7 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
         }
     }
     const size_t b64 = t64.size() * 8, b32 = t32.size() * 4;
-    CK(cudaMalloc(&b.base, b64 + b32 + 256), "base tables");
+    CK(dev_alloc(&b.base, b64 + b32 + 256), "base tables");
     CK(cudaMemcpy(b.base, t64.data(), b64, cudaMemcpyHostToDevice), "base tables");
     CK(cudaMemcpy((char *)b.base + b64, t32.data(), b32, cudaMemcpyHostToDevice), "base tables");
     const double *p64 = (const double *)b.base;
@@ -452,23 +478,23 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
 
     // state registers and scratch
     const size_t np = (size_t)x.np;
-    cudaError_t e = cudaMalloc(&b.Q, (b.mixed ? 5 : 15) * np * sizeof(double));
+    cudaError_t e = dev_alloc((void **)&b.Q, (b.mixed ? 5 : 15) * np * sizeof(double));
     if (e != cudaSuccess) {
         b.Q = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "state registers");
     }
-    e = cudaMalloc(&b.W, (b.mixed ? 12 : 6) * np * esize(ctx));
+    e = dev_alloc(&b.W, (b.mixed ? 12 : 6) * np * esize(ctx));
     if (e != cudaSuccess) {
         b.W = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "primitive buffer");
     }
-    e = cudaMalloc(&b.R, (b.mixed ? 15 : 5) * np * esize(ctx));
+    e = dev_alloc(&b.R, (b.mixed ? 15 : 5) * np * esize(ctx));
     if (e != cudaSuccess) {
         b.R = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA, "right-hand-side buffer");
     }
     if (d.visc_compact) {
-        e = cudaMalloc(&b.Gv, 12 * np * esize(ctx));
+        e = dev_alloc(&b.Gv, 12 * np * esize(ctx));
         if (e != cudaSuccess) {
             b.Gv = nullptr;
             return fail(ctx, e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA,
@@ -476,7 +502,7 @@ nopcs_status setup_box(nopcs_ctx *ctx, BoxRes &b)
         }
     }
     b.nblk_diag = diag_blocks(x.np);
-    CK(cudaMalloc(&b.partial, ((size_t)b.nblk_diag * 10 + 16) * sizeof(double)), "diagnostics scratch");
+    CK(dev_alloc((void **)&b.partial, ((size_t)b.nblk_diag * 10 + 16) * sizeof(double)), "diagnostics scratch");
     b.diag_out = b.partial + (size_t)b.nblk_diag * 10;
     CK(launch_initial_state(x, d.seed, d.perturb_amp, b.Qn(), ctx->stream), "initial state");
     CK(refresh_mixed(b, ctx->stream), "initial state");
@@ -680,30 +706,95 @@ cudaError_t enqueue_step(nopcs_ctx *ctx, BoxRes &b, cudaStream_t st)
     return cudaSuccess;
 }
 
-nopcs_status check_box(nopcs_ctx *ctx, int box)
+// Every entry point that takes a context runs on the context's device: a
+// caller that switched devices gets NOPCS_EINVAL, not launches on another GPU.
+nopcs_status check_ctx(nopcs_ctx *ctx)
 {
     if (!ctx) return NOPCS_EINVAL;
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
+    if (dev != ctx->device)
+        return fail(ctx, NOPCS_EINVAL,
+                    "the current CUDA device (" + std::to_string(dev) + ") is not the context's device (" +
+                        std::to_string(ctx->device) + "); call cudaSetDevice first");
+    return NOPCS_OK;
+}
+
+nopcs_status check_box(nopcs_ctx *ctx, int box)
+{
+    nopcs_status s = check_ctx(ctx);
+    if (s != NOPCS_OK) return s;
     if (box < 0 || box >= (int)ctx->boxes.size()) return fail(ctx, NOPCS_EINVAL, "box index out of range");
     return NOPCS_OK;
+}
+
+// one NOHAP first derivative in the form chosen for the box and axis
+cudaError_t first_derivative(nopcs_ctx *ctx, BoxRes &b, int axis, int dtype, const void *src, void *dst,
+                             cudaStream_t st)
+{
+    const double scale = b.dev.inv_h[axis];
+    if (dtype == 0)
+        return launch_line_field<double>(b.dop64[axis].dev, axis, b.dev.n, (const double *)src, (double *)dst, scale,
+                                         st);
+    if (b.deriv_gemm[axis])
+        return launch_gemm_field(b.gop[axis].dev, b.gemm_bf16[axis], axis, b.dev.n, (const float *)src, (float *)dst,
+                                 scale, ctx->dev_err, st);
+    if (b.deriv_band[axis])
+        return launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)src, (float *)dst, scale, st);
+    return launch_line_field<float>(b.dop32[axis].dev, axis, b.dev.n, (const float *)src, (float *)dst, scale, st);
 }
 
 }  // namespace
 
 namespace nopcs {
 
-nopcs_status ctx_derivative_operator(nopcs_ctx *ctx, int box, int axis, int dtype, const LineOpDev **op,
-                                     const int **n, long long *np, double *scale)
+nopcs_status ctx_derivative_check(nopcs_ctx *ctx, int box, int axis, int dtype, long long *np)
 {
     nopcs_status s = check_box(ctx, box);
     if (s != NOPCS_OK) return s;
     if (axis < 0 || axis > 2) return fail(ctx, NOPCS_EINVAL, "axis must be 0, 1 or 2");
     if (dtype != 0 && dtype != 1) return fail(ctx, NOPCS_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
-    BoxRes &b = ctx->boxes[box];
-    *op = dtype == 0 ? &b.dop64[axis].dev : &b.dop32[axis].dev;
-    *n = b.dev.n;
-    *np = b.dev.np;
-    *scale = b.dev.inv_h[axis];
+    *np = ctx->boxes[box].dev.np;
     return NOPCS_OK;
+}
+
+cudaError_t ctx_first_derivative(nopcs_ctx *ctx, int box, int axis, int dtype, const void *src, void *dst,
+                                 cudaStream_t st)
+{
+    return first_derivative(ctx, ctx->boxes[box], axis, dtype, src, dst, st);
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    Ledger *l = t_ledger;
+    if (l && l->limit && l->used + bytes > l->limit) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();  // an allocation failure is not sticky: clear it
+        return e;
+    }
+    if (l) {
+        l->used += bytes;
+        l->sizes[*p] = bytes;
+    }
+    return cudaSuccess;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    Ledger *l = t_ledger;
+    if (l) {
+        auto it = l->sizes.find(p);
+        if (it != l->sizes.end()) {
+            l->used -= it->second;
+            l->sizes.erase(it);
+        }
+    }
+    cudaFree(p);
 }
 
 nopcs_status ctx_error(nopcs_ctx *ctx, nopcs_status s, const char *msg) { return fail(ctx, s, msg); }
@@ -729,19 +820,24 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
     ctx->prec = prec;
     ctx->form = form;
     ctx->stream = (cudaStream_t)stream;
+    ctx->ledger.limit = g_mem_limit.load();
+    LedgerScope scope(&ctx->ledger);
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = init_line_kernels();
     if (e == cudaSuccess) e = init_visc_kernels();
     if (e == cudaSuccess && (ctx->form == NOPCS_FORM_GEMM_3XTF32 || ctx->form == NOPCS_FORM_GEMM_BF16X3 ||
                              ctx->form == NOPCS_FORM_AUTO))
         e = init_gemm_kernels();
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_err, sizeof(int));
+    // the static scratch of nopcs_derivative2_noalloc becomes resident on this
+    // device now, so that no later call loads its module
+    if (e == cudaSuccess) e = noalloc_prepare();
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->dev_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->dev_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         g_init_error = std::string("CUDA: ") + cudaGetErrorString(e);
-        delete ctx;
-        return NOPCS_ECUDA;
+        nopcs_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? NOPCS_ENOMEM : NOPCS_ECUDA;
     }
     ctx->boxes.resize(nboxes);
     for (int i = 0; i < nboxes; ++i) {
@@ -767,6 +863,11 @@ nopcs_status nopcs_init(const nopcs_box_desc *boxes, int nboxes, nopcs_precision
 void nopcs_destroy(nopcs_ctx *ctx)
 {
     if (!ctx) return;
+    // free on the context's device, whatever device the caller has current
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = -1;
+    if (cur != ctx->device) cudaSetDevice(ctx->device);
+    LedgerScope scope(&ctx->ledger);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
     for (auto st : ctx->branch) cudaStreamDestroy(st);
@@ -776,9 +877,11 @@ void nopcs_destroy(nopcs_ctx *ctx)
         cudaEventDestroy(p.b);
     }
     for (auto &b : ctx->boxes) free_box(b);
-    if (ctx->dev_err) cudaFree(ctx->dev_err);
+    if (ctx->dev_err) dev_free(ctx->dev_err);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    const int dev = ctx->device;
     delete ctx;
+    if (cur >= 0 && cur != dev) cudaSetDevice(cur);
 }
 
 const char *nopcs_last_error(const nopcs_ctx *ctx)
@@ -823,6 +926,21 @@ nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box)
     return NOPCS_OK;
 }
 
+nopcs_status nopcs_set_step(nopcs_ctx *ctx, int box, long long step)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (step < 0) return fail(ctx, NOPCS_EINVAL, "step must be >= 0");
+    ctx->boxes[box].step = step;
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_set_memory_limit(unsigned long long bytes)
+{
+    g_mem_limit.store(bytes);
+    return NOPCS_OK;
+}
+
 nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int dtype, const void *f, void *df,
                               void *stream)
 {
@@ -849,46 +967,26 @@ nopcs_status nopcs_derivative(nopcs_ctx *ctx, int box, int axis, int order, int 
         if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
         return NOPCS_OK;
     }
-    const LineOpDev &op = dtype == 0 ? b.dop64[axis].dev : b.dop32[axis].dev;
     const void *src = f;
     if (order == 2) {
         if (!b.scratch) {
-            cudaError_t e = cudaMalloc(&b.scratch, (size_t)b.dev.np * 8);
-            if (e != cudaSuccess) {
-                b.scratch = nullptr;
-                return fail(ctx, NOPCS_ENOMEM, "order-2 scratch");
-            }
+            LedgerScope scope(&ctx->ledger);
+            cudaError_t e = dev_alloc(&b.scratch, (size_t)b.dev.np * 8);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "order-2 scratch");
         }
-        cudaError_t e;
-        if (dtype == 1 && b.deriv_gemm[axis])
-            e = launch_gemm_field(b.gop[axis].dev, b.gemm_bf16[axis], axis, b.dev.n, (const float *)f,
-                                  (float *)b.scratch, scale, ctx->dev_err, st);
-        else if (dtype == 1 && b.deriv_band[axis])
-            e = launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)f, (float *)b.scratch, scale, st);
-        else if (dtype == 0)
-            e = launch_line_field<double>(op, axis, b.dev.n, (const double *)f, (double *)b.scratch, scale, st);
-        else
-            e = launch_line_field<float>(op, axis, b.dev.n, (const float *)f, (float *)b.scratch, scale, st);
+        cudaError_t e = first_derivative(ctx, b, axis, dtype, f, b.scratch, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
         src = b.scratch;
     }
-    cudaError_t e;
-    if (dtype == 1 && b.deriv_gemm[axis])
-        e = launch_gemm_field(b.gop[axis].dev, b.gemm_bf16[axis], axis, b.dev.n, (const float *)src, (float *)df,
-                              scale, ctx->dev_err, st);
-    else if (dtype == 1 && b.deriv_band[axis])
-        e = launch_band_field(b.bop[axis], axis, b.dev.n, (const float *)src, (float *)df, scale, st);
-    else if (dtype == 0)
-        e = launch_line_field<double>(op, axis, b.dev.n, (const double *)src, (double *)df, scale, st);
-    else
-        e = launch_line_field<float>(op, axis, b.dev.n, (const float *)src, (float *)df, scale, st);
+    cudaError_t e = first_derivative(ctx, b, axis, dtype, src, df, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "derivative");
     return NOPCS_OK;
 }
 
 nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps)
 {
-    if (!ctx) return NOPCS_EINVAL;
+    nopcs_status s0 = check_ctx(ctx);
+    if (s0 != NOPCS_OK) return s0;
     if (nsteps < 0) return fail(ctx, NOPCS_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return NOPCS_OK;
     if (!ctx->profiling && !ctx->step_exec) {
@@ -1023,7 +1121,8 @@ nopcs_status nopcs_plane_fields(nopcs_ctx *ctx, int box, int axis, int index, in
 
 nopcs_status nopcs_synchronize(nopcs_ctx *ctx)
 {
-    if (!ctx) return NOPCS_EINVAL;
+    nopcs_status s0 = check_ctx(ctx);
+    if (s0 != NOPCS_OK) return s0;
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     CK(cudaDeviceSynchronize(), "synchronize");
     int flag = 0;
@@ -1037,7 +1136,8 @@ nopcs_status nopcs_synchronize(nopcs_ctx *ctx)
 
 nopcs_status nopcs_set_profiling(nopcs_ctx *ctx, int on)
 {
-    if (!ctx) return NOPCS_EINVAL;
+    nopcs_status s0 = check_ctx(ctx);
+    if (s0 != NOPCS_OK) return s0;
     if (on && ctx->pool.empty()) {
         ctx->pool.resize(4096);
         for (auto &p : ctx->pool) {
@@ -1055,7 +1155,8 @@ nopcs_status nopcs_set_profiling(nopcs_ctx *ctx, int on)
 
 nopcs_status nopcs_profile_read(nopcs_ctx *ctx, double *ms, long long *launches, int reset)
 {
-    if (!ctx) return NOPCS_EINVAL;
+    nopcs_status s0 = check_ctx(ctx);
+    if (s0 != NOPCS_OK) return s0;
     CK(cudaStreamSynchronize(ctx->stream), "profile read");
     harvest(ctx);
     for (int k = 0; k < NOPCS_NUM_KERNELS; ++k) {

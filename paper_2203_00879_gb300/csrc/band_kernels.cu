@@ -188,7 +188,7 @@ cudaError_t BandBuf::upload()
     const BandHost &h = host;
     const size_t nw = h.wrow.size();
     const size_t bytes = 2 * nw * sizeof(int) + nw * (size_t)h.W * sizeof(float) + (size_t)BT * sizeof(float) + 64;
-    cudaError_t e = cudaMalloc(&mem, bytes);
+    cudaError_t e = dev_alloc(&mem, bytes);
     if (e != cudaSuccess) {
         mem = nullptr;
         return e;
@@ -217,7 +217,7 @@ cudaError_t BandBuf::upload()
 
 void BandBuf::release()
 {
-    if (mem) cudaFree(mem);
+    if (mem) dev_free(mem);
     mem = nullptr;
 }
 

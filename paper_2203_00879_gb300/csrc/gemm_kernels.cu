@@ -180,7 +180,10 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
     float c0 = 0.0f;
     if (AXIS != 0 && tid < nl) c0 = f[gbase + (long long)s * srow + tid];
     const uint32_t idesc = BF ? idesc_bf16(npad) : idesc_tf32(npad);
+    // ok: every bounded wait of this thread so far succeeded; issued: the last
+    // chunk whose MMAs were issued and committed (-1: none)
     bool ok = true;
+    int issued = -1;
     for (int c = 0; c < nchunk; ++c) {
         const int st = c & 1;
         unsigned char *A0 = smraw + st * stage_bytes;  // part q at A0 + q ABYTES
@@ -280,7 +283,14 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
         // generic-proxy shared stores -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        // the block agrees whether every wait so far succeeded; after a wait
+        // gave up, no further MMA is issued (the stores above may have hit a
+        // stage still being read: shared memory only, and the result is
+        // discarded)
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int ksteps = min(KC, kpad - k0) / KMMA;
@@ -315,13 +325,18 @@ __global__ void __launch_bounds__(GM) gemm_deriv_kernel(const GemmOpDev op, int 
                              smem_u32(mbar + st))
                          : "memory");
         }
+        issued = c;
     }
-    // the last commit covers every MMA issued before it
-    {
-        const int c = nchunk - 1;
+    // The last commit covers every MMA issued before it.  On the normal path
+    // this is the wait for the result; after a wait gave up it drains the
+    // MMAs still in flight (again bounded) before the accumulator columns are
+    // freed.  Chunk `issued`'s barrier had its previous phase (chunk
+    // issued - 2) observed at the start of chunk `issued`, so its parity is
+    // unambiguous.
+    if (issued >= 0) {
         bool done = false;
         for (long long it = 0; it < WAIT_ITERS && !done; ++it)
-            done = mbar_try_wait(smem_u32(mbar + (c & 1)), (uint32_t)((c >> 1) & 1));
+            done = mbar_try_wait(smem_u32(mbar + (issued & 1)), (uint32_t)((issued >> 1) & 1));
         ok = ok && done;
     }
     const int all_ok = __syncthreads_and(ok ? 1 : 0);
@@ -424,7 +439,7 @@ cudaError_t GemmOpBuf::upload()
     const size_t nrec = host.rec.size() * sizeof(int), nf = host.hi.size() * sizeof(float);
     const size_t n16 = host.b16[0].size() * sizeof(uint16_t);
     const size_t o_hi = al(nrec), o_lo = o_hi + al(nf), o_b16 = o_lo + al(nf);
-    cudaError_t e = cudaMalloc(&mem, o_b16 + 3 * al(n16) + 16);
+    cudaError_t e = dev_alloc(&mem, o_b16 + 3 * al(n16) + 16);
     if (e != cudaSuccess) {
         mem = nullptr;
         return e;
@@ -450,7 +465,7 @@ cudaError_t GemmOpBuf::upload()
 
 void GemmOpBuf::release()
 {
-    if (mem) cudaFree(mem);
+    if (mem) dev_free(mem);
     mem = nullptr;
 }
 

@@ -14,6 +14,9 @@
 // In host code `g_noalloc_scratch` only names a host-side stand-in for the
 // array; its device address is obtained with cudaGetSymbolAddress, once per
 // device, with that device current, and that address is what the kernels get.
+// nopcs_init does that lookup on its device (noalloc_prepare), which also
+// loads this file's module there: from then on the 16 MiB are resident on
+// that device, and no call of the entry point loads a module or allocates.
 #include <mutex>
 
 #include "nopcs_internal.cuh"
@@ -48,17 +51,24 @@ cudaError_t scratch_address(void **out)
 
 }  // namespace
 
+namespace nopcs {
+
+cudaError_t noalloc_prepare()
+{
+    void *p = nullptr;
+    return scratch_address(&p);
+}
+
+}  // namespace nopcs
+
 using namespace nopcs;
 
 extern "C" nopcs_status nopcs_derivative2_noalloc(nopcs_ctx *ctx, int box, int axis, int dtype, const void *f,
                                                   void *df, void *stream)
 {
     if (!ctx) return NOPCS_EINVAL;
-    const LineOpDev *op = nullptr;
-    const int *n = nullptr;
     long long np = 0;
-    double scale = 0.0;
-    nopcs_status s = ctx_derivative_operator(ctx, box, axis, dtype, &op, &n, &np, &scale);
+    nopcs_status s = ctx_derivative_check(ctx, box, axis, dtype, &np);
     if (s != NOPCS_OK) return s;
     if (!f || !df) return ctx_error(ctx, NOPCS_EINVAL, "null field pointer");
     const size_t es = dtype == 0 ? 8 : 4;
@@ -73,16 +83,11 @@ extern "C" nopcs_status nopcs_derivative2_noalloc(nopcs_ctx *ctx, int box, int a
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) return ctx_error(ctx, NOPCS_ECUDA, "nopcs_derivative2_noalloc: scratch address");
     cudaStream_t st = (cudaStream_t)stream;
-    // pass 1 writes every element of the scratch it uses, so nothing needs clearing
-    if (dtype == 0) {
-        e = launch_line_field<double>(*op, axis, n, (const double *)f, (double *)scratch, scale, st);
-        if (e == cudaSuccess)
-            e = launch_line_field<double>(*op, axis, n, (const double *)scratch, (double *)df, scale, st);
-    } else {
-        e = launch_line_field<float>(*op, axis, n, (const float *)f, (float *)scratch, scale, st);
-        if (e == cudaSuccess)
-            e = launch_line_field<float>(*op, axis, n, (const float *)scratch, (float *)df, scale, st);
-    }
+    // the two passes of nopcs_derivative(order = 2), in the same form per axis
+    // (Thomas, banded or tensor-core); pass 1 writes every element of the
+    // scratch that pass 2 reads, so nothing needs clearing
+    e = ctx_first_derivative(ctx, box, axis, dtype, f, scratch, st);
+    if (e == cudaSuccess) e = ctx_first_derivative(ctx, box, axis, dtype, scratch, df, st);
     if (e != cudaSuccess) return ctx_error(ctx, NOPCS_ECUDA, "nopcs_derivative2_noalloc: launch failed");
     return NOPCS_OK;
 }

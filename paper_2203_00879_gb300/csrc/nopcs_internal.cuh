@@ -167,6 +167,26 @@ struct BoxDev {
     int *err;          // device error word: set by a kernel whose bounded wait gave up
 };
 
+// Mixed form: the FP32 primitives W = (rho', u, v, w, p', H') of a state from
+// its FP32 deviation from the hydrostatic base, D = (rho - rho_b, m_x, m_y,
+// m_z, E - E_b), with p' = (gamma - 1)(E' - rho |V|^2 / 2) and H' = E' + p'.
+// Every kernel that forms the primitives of a stored state uses this one
+// function, so a state has the same FP32 primitives whichever kernel computed
+// them (a run resumed from nopcs_set_state continues bit for bit).
+__device__ __forceinline__ void prim_from_deviation(float rho_b, float gm1, const float D[5], float Wv[6])
+{
+    const float ir = __fdividef(1.0f, rho_b + D[0]);
+    const float u = D[1] * ir, v = D[2] * ir, w = D[3] * ir;
+    const float ke = 0.5f * (D[1] * u + D[2] * v + D[3] * w);
+    const float pd = gm1 * (D[4] - ke);
+    Wv[0] = D[0];
+    Wv[1] = u;
+    Wv[2] = v;
+    Wv[3] = w;
+    Wv[4] = pd;
+    Wv[5] = D[4] + pd;
+}
+
 // ---- launchers (line_kernels.cu) -------------------------------------------
 // Raises the dynamic shared-memory limit of every line-kernel instantiation
 // on the current device (called once per context, outside stream capture).
@@ -252,12 +272,28 @@ cudaError_t launch_diagnostics(const BoxDev &bx, const double *Q, double *partia
                                double *out, cudaStream_t st);
 int diag_blocks(long long np);
 
+// ---- device memory ------------------------------------------------------------
+// Every device allocation of the library goes through these two calls.  While
+// an entry point of a context runs, they count its bytes against the process
+// limit set with nopcs_set_memory_limit; an allocation beyond it fails with
+// cudaErrorMemoryAllocation, which the entry points report as NOPCS_ENOMEM.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+
 // ---- context access for entry points outside api.cu ------------------------
-// Operator and geometry of box `box` for a derivative along `axis` in `dtype`
-// (0 f64, 1 f32); validates the box index.  Returns NOPCS_OK or sets the
-// context's error message.
-nopcs_status ctx_derivative_operator(nopcs_ctx *ctx, int box, int axis, int dtype, const LineOpDev **op,
-                                     const int **n, long long *np, double *scale);
+// Validates a derivative request on box `box` (the context's device current,
+// the box index, axis 0..2, dtype 0 f64 / 1 f32) and gives the box's point
+// count.  Returns NOPCS_OK or sets the context's error message.
+nopcs_status ctx_derivative_check(nopcs_ctx *ctx, int box, int axis, int dtype, long long *np);
+// One NOHAP first derivative along `axis` of a field of box `box`, dst =
+// (1/h) L src, in the form nopcs_derivative uses for that box and axis (FP32:
+// Thomas, banded or a tensor-core form as chosen at nopcs_init; FP64: Thomas).
+// Arguments as validated by ctx_derivative_check.
+cudaError_t ctx_first_derivative(nopcs_ctx *ctx, int box, int axis, int dtype, const void *src, void *dst,
+                                 cudaStream_t st);
 nopcs_status ctx_error(nopcs_ctx *ctx, nopcs_status s, const char *msg);
+// Looks up, on the current device, the device address of the static scratch
+// array of nopcs_derivative2_noalloc (which loads the array's module there).
+cudaError_t noalloc_prepare();
 
 }  // namespace nopcs

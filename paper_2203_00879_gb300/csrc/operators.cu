@@ -480,7 +480,7 @@ cudaError_t LineOpBuf::upload()
     size_t o_sub = 0, o_c64 = al(nsub_b), o_c32 = o_c64 + al(nc * 8), o_cp64 = o_c32 + al(nc * 4),
            o_inv64 = o_cp64 + al(nm * 8), o_cp32 = o_inv64 + al(nm * 8), o_inv32 = o_cp32 + al(nm * 4),
            tot = o_inv32 + al(nm * 4);
-    cudaError_t e = cudaMalloc(&mem, tot);
+    cudaError_t e = dev_alloc(&mem, tot);
     if (e != cudaSuccess) {
         mem = nullptr;
         return e;
@@ -527,7 +527,7 @@ cudaError_t LineOpBuf::upload()
 
 void LineOpBuf::release()
 {
-    if (mem) cudaFree(mem);
+    if (mem) dev_free(mem);
     mem = nullptr;
 }
 

@@ -44,25 +44,17 @@ __device__ __forceinline__ void prep_point(const BoxDev &bx, long long p, int kg
         W[4 * np + p] = pr - bx.p_b64[kg];
         W[5 * np + p] = E + pr - bx.H_b64[kg];
     } else {
-        const float rd = (float)(r - bx.rho_b64[kg]);
-        const float Ed = (float)(E - bx.E_b64[kg]);
-        const float rf = (float)r;
-        const float ir = 1.0f / rf;
-        const float u = (float)mx * ir, v = (float)my * ir, w = (float)mz * ir;
-        const float ke = 0.5f * rf * (u * u + v * v + w * w);
-        const float pd = (float)(bx.gamma - 1.0) * (Ed - ke);
-        W[p] = rd;
-        W[np + p] = u;
-        W[2 * np + p] = v;
-        W[3 * np + p] = w;
-        W[4 * np + p] = pd;
-        W[5 * np + p] = Ed + pd;
-        if (Dn) {  // deviation of the state from the hydrostatic base (mixed form)
-            Dn[p] = rd;
-            Dn[np + p] = (float)mx;
-            Dn[2 * np + p] = (float)my;
-            Dn[3 * np + p] = (float)mz;
-            Dn[4 * np + p] = Ed;
+        // deviation of the state from the hydrostatic base (mixed form), then
+        // the primitives from it exactly as the stage kernels form them
+        const float D[5] = {(float)(r - bx.rho_b64[kg]), (float)mx, (float)my, (float)mz,
+                            (float)(E - bx.E_b64[kg])};
+        float Wv[6];
+        prim_from_deviation(bx.rho_b32[kg], (float)(bx.gamma - 1.0), D, Wv);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) W[k * np + p] = Wv[k];
+        if (Dn) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Dn[k * np + p] = D[k];
         }
     }
 }
@@ -145,16 +137,13 @@ __device__ void set_wall_node(const BoxDev &bx, double *Q, const int c[3], float
     Q[4 * np + i] = Q[i] * Tw * bx.cE;
     if (Dn) {
         const int kg = c[bx.ga];
-        const float rd = (float)(Q[i] - bx.rho_b64[kg]);
-        const float Ed = (float)(Q[4 * np + i] - bx.E_b64[kg]);
-        const float pd = (float)(bx.gamma - 1.0) * Ed;
-        Dn[i] = rd;
-        Dn[np + i] = Dn[2 * np + i] = Dn[3 * np + i] = 0.0f;
-        Dn[4 * np + i] = Ed;
-        Wf[i] = rd;
-        Wf[np + i] = Wf[2 * np + i] = Wf[3 * np + i] = 0.0f;
-        Wf[4 * np + i] = pd;
-        Wf[5 * np + i] = Ed + pd;
+        const float D[5] = {(float)(Q[i] - bx.rho_b64[kg]), 0.0f, 0.0f, 0.0f, (float)(Q[4 * np + i] - bx.E_b64[kg])};
+        float Wv[6];
+        prim_from_deviation(bx.rho_b32[kg], (float)(bx.gamma - 1.0), D, Wv);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Dn[k * np + i] = D[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Wf[k * np + i] = Wv[k];
     }
 }
 

@@ -293,17 +293,10 @@ __device__ __forceinline__ void flux_z(const VArgs<T> &a, const Stencil<T, EDGE>
 // primitives of a stage state from its FP32 deviation D = (rho', m_x, m_y, m_z, E')
 __device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, int p, int kg, const float D[5])
 {
-    const float rho = a.rho_b[kg] + D[0];
-    const float ir = __fdividef(1.0f, rho);
-    const float u = D[1] * ir, v = D[2] * ir, w = D[3] * ir;
-    const float ke = 0.5f * (D[1] * u + D[2] * v + D[3] * w);
-    const float pd = a.gm1 * (D[4] - ke);
-    a.Wn[0][p] = D[0];
-    a.Wn[1][p] = u;
-    a.Wn[2][p] = v;
-    a.Wn[3][p] = w;
-    a.Wn[4][p] = pd;
-    a.Wn[5][p] = D[4] + pd;
+    float Wv[6];
+    prim_from_deviation(a.rho_b[kg], a.gm1, D, Wv);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.Wn[k][p] = Wv[k];
 }
 
 // Mixed form of the classical RK4 stage.  The slopes are FP32 (they are FP32

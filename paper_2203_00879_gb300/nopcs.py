@@ -55,6 +55,8 @@ _L.nopcs_last_error.restype = C.c_char_p
 _L.nopcs_set_state.argtypes = [_vp, _i, _vp]
 _L.nopcs_get_state.argtypes = [_vp, _i, _vp]
 _L.nopcs_reset_state.argtypes = [_vp, _i]
+_L.nopcs_set_step.argtypes = [_vp, _i, C.c_longlong]
+_L.nopcs_set_memory_limit.argtypes = [C.c_ulonglong]
 _L.nopcs_derivative.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp, _vp]
 _L.nopcs_derivative2_noalloc.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp]
 _L.nopcs_rk_step.argtypes = [_vp, _i]
@@ -72,7 +74,8 @@ _L.nopcs_operator_rows.argtypes = [_i, _i, _i, _d, _d, C.POINTER(_i), C.POINTER(
 _L.nopcs_operator_apply.argtypes = [_i, _i, _i, _d, _d, C.c_void_p, C.c_void_p]
 _L.nopcs_plane_fields.argtypes = [_vp, _i, _i, _i, _i, _vp]
 _L.nopcs_band_apply.argtypes = [_i, _i, _d, _d, C.c_void_p, C.c_void_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]
-for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_plane_fields", "nopcs_init", "nopcs_set_state", "nopcs_get_state", "nopcs_reset_state", "nopcs_derivative",
+for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_plane_fields", "nopcs_init", "nopcs_set_state",
+              "nopcs_get_state", "nopcs_reset_state", "nopcs_set_step", "nopcs_set_memory_limit", "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
               "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows", "nopcs_box_info"):
@@ -129,6 +132,16 @@ def nopcs_get_state(ctx, box: int, q_ptr: int) -> None:
 
 def nopcs_reset_state(ctx, box: int) -> None:
     _check(ctx, _L.nopcs_reset_state(ctx, box))
+
+
+def nopcs_set_step(ctx, box: int, step: int) -> None:
+    _check(ctx, _L.nopcs_set_step(ctx, box, step))
+
+
+def nopcs_set_memory_limit(nbytes: int) -> None:
+    """Process-wide cap on the device bytes of each context created
+    afterwards (0: no cap)."""
+    _check(None, _L.nopcs_set_memory_limit(nbytes))
 
 
 def nopcs_derivative(ctx, box: int, axis: int, order: int, dtype: int, f_ptr: int, df_ptr: int,

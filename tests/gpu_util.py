@@ -51,3 +51,16 @@ def state_err(Q, ref, p):
     out = d / np.abs(ref).reshape(5, -1).max(axis=1)
     out[1:4] = d[1:4] / mscale
     return out
+
+
+def dist_rel(Q, ref, Q0):
+    """Disturbance-relative L-inf error per conserved variable:
+    max |Q - ref| / max |ref - Q0|, with Q0 the initial state both runs
+    started from.  For rho and E the flow changes only ~1e-4 of the field, so
+    this is the figure that shows an error of the size of the flow itself."""
+    Q = np.asarray(Q, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    Q0 = np.asarray(Q0, dtype=np.float64)
+    d = np.abs(Q - ref).reshape(Q.shape[0], -1).max(axis=1)
+    s = np.abs(ref - Q0).reshape(Q.shape[0], -1).max(axis=1)
+    return d / np.where(s == 0, 1.0, s)

@@ -1,0 +1,160 @@
+"""Failure behaviour and checkpoint/resume of the C ABI, made on the host:
+a non-finite state written through nopcs_set_state, an allocation cap that
+nopcs_init cannot meet, a run split at a checkpoint, a call from the wrong
+device, and the library's initial state against the SplitMix64 published test
+vector.  No test here faults, traps or hangs the GPU."""
+import numpy as np
+import pytest
+
+import nopcs_synth as S
+from gpu_util import binding, stream_ptr, to_dev
+from test_splitmix64 import expected_velocity, shifted_seed
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(N, ctx, p, box=0):
+    import torch
+    Q = torch.empty((5, p["n"][2], p["n"][1], p["n"][0]), dtype=torch.float64, device="cuda")
+    N.nopcs_get_state(ctx, box, Q.data_ptr())
+    return Q.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_state_is_reported_unstable(prec, bad):
+    N = binding()
+    p = S.box_params((20, 18, 22), sub_n=(8, 8, 8))
+    ctx = N.nopcs_init([p], prec=prec, stream=stream_ptr())
+    try:
+        assert N.nopcs_diagnostics(ctx, 0)["nonfinite"] == 0
+        Q = _state(N, ctx, p)
+        Q[4, 11, 9, 7] = bad
+        N.nopcs_set_state(ctx, 0, to_dev(Q).data_ptr())
+        with pytest.raises(N.NopcsError) as ei:
+            N.nopcs_diagnostics(ctx, 0)
+        assert ei.value.status == N.NOPCS_EUNSTABLE
+        d = N.nopcs_diagnostics(ctx, 0, allow_unstable=True)
+        assert d["nonfinite"] == 1
+        # the context stays usable: a finite state clears the flag
+        Q[4, 11, 9, 7] = 1.0 / (p["gamma"] - 1) / (p["gamma"] * p["M"] ** 2)
+        N.nopcs_set_state(ctx, 0, to_dev(Q).data_ptr())
+        assert N.nopcs_diagnostics(ctx, 0)["nonfinite"] == 0
+    finally:
+        N.nopcs_destroy(ctx)
+
+
+def _free_bytes():
+    """Free device memory as the driver reports it, plus what torch's caching
+    allocator holds (so tensors created and freed in between do not count)."""
+    import torch
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0] + torch.cuda.memory_reserved()
+
+
+def test_memory_limit_gives_enomem_and_leaks_nothing():
+    N = binding()
+    p = S.box_params((96, 80, 72), sub_n=(32, 32, 32))
+    # a first context loads every module and settles the driver's own pools
+    c0 = N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_THOMAS, stream=stream_ptr())
+    N.nopcs_destroy(c0)
+    free0 = _free_bytes()
+    np_ = 96 * 80 * 72
+    try:
+        for limit in (1 << 20, 100 * np_):  # below the tables, below the registers (148 B/pt)
+            N.nopcs_set_memory_limit(limit)
+            with pytest.raises(N.NopcsError) as ei:
+                N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_THOMAS, stream=stream_ptr())
+            assert ei.value.status == N.NOPCS_ENOMEM, str(ei.value)
+            assert _free_bytes() == free0
+        # enough for the context, not for the order-2 scratch (8 B/pt)
+        N.nopcs_set_memory_limit(155 * np_)
+        ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_THOMAS, stream=stream_ptr())
+        try:
+            import torch
+            f = torch.zeros((72, 80, 96), dtype=torch.float32, device="cuda")
+            out = torch.empty_like(f)
+            N.nopcs_derivative(ctx, 0, 0, 1, 1, f.data_ptr(), out.data_ptr(), stream_ptr())
+            with pytest.raises(N.NopcsError) as ei:
+                N.nopcs_derivative(ctx, 0, 0, 2, 1, f.data_ptr(), out.data_ptr(), stream_ptr())
+            assert ei.value.status == N.NOPCS_ENOMEM
+            N.nopcs_rk_step(ctx, 1)  # still usable
+            N.nopcs_synchronize(ctx)
+            del f, out
+        finally:
+            N.nopcs_destroy(ctx)
+    finally:
+        N.nopcs_set_memory_limit(0)
+    ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, form=N.NOPCS_FORM_THOMAS, stream=stream_ptr())
+    N.nopcs_destroy(ctx)
+    assert _free_bytes() == free0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_resume_is_bitwise(prec):
+    """k + m steps in one run equal k steps, a checkpoint (state and step
+    counter), a fresh context restored from it, and m more steps: bit for bit,
+    with the filter firing inside both halves."""
+    N = binding()
+    p = S.box_params((30, 28, 26), sub_n=(12, 12, 12), filter_every=3, perturb_amp=1e-3, seed=8)
+    k, m = 4, 5
+    ctx = N.nopcs_init([p], prec=prec, stream=stream_ptr())
+    try:
+        N.nopcs_rk_step(ctx, k)
+        Qk = _state(N, ctx, p)
+        step_k = N.nopcs_diagnostics(ctx, 0)["step"]
+        N.nopcs_rk_step(ctx, m)
+        Qa = _state(N, ctx, p)
+    finally:
+        N.nopcs_destroy(ctx)
+    assert step_k == k
+    ctx = N.nopcs_init([p], prec=prec, stream=stream_ptr())
+    try:
+        N.nopcs_set_state(ctx, 0, to_dev(Qk).data_ptr())
+        N.nopcs_set_step(ctx, 0, step_k)
+        N.nopcs_rk_step(ctx, m)
+        Qb = _state(N, ctx, p)
+        assert N.nopcs_diagnostics(ctx, 0)["step"] == k + m
+    finally:
+        N.nopcs_destroy(ctx)
+    assert np.array_equal(Qa, Qb)
+    assert not np.array_equal(Qa, Qk)
+
+
+def test_calls_from_another_device_are_rejected():
+    import torch
+    N = binding()
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    p = S.box_params((16, 16, 16), sub_n=(8, 8, 8))
+    torch.cuda.set_device(0)
+    ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED)
+    try:
+        torch.cuda.set_device(1)
+        with pytest.raises(N.NopcsError) as ei:
+            N.nopcs_rk_step(ctx, 1)
+        assert ei.value.status == N.NOPCS_EINVAL and "device" in str(ei.value)
+    finally:
+        N.nopcs_destroy(ctx)  # frees on device 0 and switches back
+        assert torch.cuda.current_device() == 1
+        torch.cuda.set_device(0)
+
+
+def test_initial_state_draws_the_published_splitmix_vector():
+    """The library's generator against the SplitMix64 published test vector:
+    with the seed shifted so that node p draws values 0..4 of the stream seeded
+    with 1234567, node p's u, v, w and node p+1's u, v are those values."""
+    N = binding()
+    n = (9, 8, 7)
+    i, j, k = 3, 4, 2
+    pidx = i + n[0] * (j + n[1] * k)
+    amp = 1e-3
+    p = S.box_params(n, sub_n=(0, 0, 0), perturb_amp=amp, seed=shifted_seed(3 * pidx))
+    ctx = N.nopcs_init([p], prec=N.NOPCS_FP64, stream=stream_ptr())
+    try:
+        Q = _state(N, ctx, p)
+    finally:
+        N.nopcs_destroy(ctx)
+    V = [Q[c + 1, k, j, i] / Q[0, k, j, i] for c in range(3)] + \
+        [Q[c + 1, k, j, i + 1] / Q[0, k, j, i + 1] for c in range(2)]
+    np.testing.assert_allclose(V, expected_velocity(amp), rtol=1e-14, atol=0)

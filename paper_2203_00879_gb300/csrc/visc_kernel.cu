@@ -73,44 +73,164 @@ __device__ __forceinline__ T node_temperature(const VArgs<T> &a, int kg, T w0, T
     }
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p)
+// ---- four ring fields per node ------------------------------------------------
+// A ring node holds (u, v, w, T) as one 16-byte (FP32) or 32-byte (FP64)
+// vector, so the gradient of all four fields along an axis is two vector
+// loads; the FP32 arithmetic on such vectors runs as packed FP32x2 operations.
+struct alignas(32) dbl4 {
+    double x, y, z, w;
+};
+template <typename T>
+struct V4T;
+template <>
+struct V4T<float> {
+    using type = float4;
+};
+template <>
+struct V4T<double> {
+    using type = dbl4;
+};
+template <typename T>
+using V4 = typename V4T<T>::type;
+
+// Scalar arithmetic in a fixed order (no contraction into FMAs the compiler
+// might choose differently in different places): a flux evaluated at the same
+// node from the same inputs gives the same bits in every block that needs it.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+__device__ __forceinline__ float2 lo2(const float4 &a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(const float4 &a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 cat4(float2 l, float2 h) { return make_float4(l.x, l.y, h.x, h.y); }
+
+// a - b (as fma(b, -1, a): one rounding, the same as a subtraction)
+__device__ __forceinline__ float4 v_sub(const float4 &a, const float4 &b)
 {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    return cat4(__ffma2_rn(lo2(b), m1, lo2(a)), __ffma2_rn(hi2(b), m1, hi2(a)));
+}
+__device__ __forceinline__ float4 v_add(const float4 &a, const float4 &b)
+{
+    return cat4(__fadd2_rn(lo2(a), lo2(b)), __fadd2_rn(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 v_mul(const float4 &a, float s)
+{
+    const float2 s2 = make_float2(s, s);
+    return cat4(__fmul2_rn(lo2(a), s2), __fmul2_rn(hi2(a), s2));
+}
+// a s + c
+__device__ __forceinline__ float4 v_fma(const float4 &a, float s, const float4 &c)
+{
+    const float2 s2 = make_float2(s, s);
+    return cat4(__ffma2_rn(lo2(a), s2, lo2(c)), __ffma2_rn(hi2(a), s2, hi2(c)));
+}
+__device__ __forceinline__ dbl4 v_sub(const dbl4 &a, const dbl4 &b)
+{
+    return dbl4{__dadd_rn(a.x, -b.x), __dadd_rn(a.y, -b.y), __dadd_rn(a.z, -b.z), __dadd_rn(a.w, -b.w)};
+}
+__device__ __forceinline__ dbl4 v_add(const dbl4 &a, const dbl4 &b)
+{
+    return dbl4{__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z), __dadd_rn(a.w, b.w)};
+}
+__device__ __forceinline__ dbl4 v_mul(const dbl4 &a, double s)
+{
+    return dbl4{__dmul_rn(a.x, s), __dmul_rn(a.y, s), __dmul_rn(a.z, s), __dmul_rn(a.w, s)};
+}
+__device__ __forceinline__ dbl4 v_fma(const dbl4 &a, double s, const dbl4 &c)
+{
+    return dbl4{__fma_rn(a.x, s, c.x), __fma_rn(a.y, s, c.y), __fma_rn(a.z, s, c.z), __fma_rn(a.w, s, c.w)};
 }
 
-// Ask L2 for what the RK update of node p will load: its right-hand side and
-// (mixed form) K, D_n and, in stage 4, Q_n.  Issued a plane ahead, these take
-// the DRAM latency off the update, which runs after the plane's barrier; an L2
-// prefetch holds no register (loading them into registers before the flux
-// phase instead was slower).
-template <typename T>
-__device__ __forceinline__ void prefetch_node(const VArgs<T> &a, int p)
+// second-order differences of a ring vector: central (p+ - p-) / (2h) and the
+// one-sided (-3 p0 + 4 p1 - p2) / (2h) at a low wall, (3 p0 - 4 p-1 + p-2) /
+// (2h) at a high wall (ih = 1 / (2h))
+template <typename V, typename T>
+__device__ __forceinline__ V d_central(const V &pp, const V &pm, T ih)
 {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) prefetch_l2(a.R[k] + p);
+    return v_mul(v_sub(pp, pm), ih);
+}
+template <typename V, typename T>
+__device__ __forceinline__ V d_low(const V &p0, const V &p1, const V &p2, T ih)
+{
+    return v_mul(v_sub(v_fma(p1, T(4), v_mul(p0, T(-3))), p2), ih);
+}
+template <typename V, typename T>
+__device__ __forceinline__ V d_high(const V &p0, const V &pm1, const V &pm2, T ih)
+{
+    return v_mul(v_add(v_fma(pm1, T(-4), v_mul(p0, T(3))), pm2), ih);
+}
+
+// ---- L2 prefetch ---------------------------------------------------------------
+// One bulk prefetch of the bytes [p, p + bytes) of a field that spans
+// [f0, f1), clipped to 16-byte boundaries inside the field (a bulk prefetch
+// takes 16-byte aligned addresses and sizes).  One thread asks for a whole
+// tile row this way, instead of every thread issuing a prefetch per value.
+__device__ __forceinline__ void bulk_prefetch(const void *f0, const void *f1, const void *p, unsigned bytes)
+{
+    const unsigned long long lo = ((unsigned long long)f0 + 15) & ~15ull, hi = (unsigned long long)f1 & ~15ull;
+    unsigned long long a = (unsigned long long)p & ~15ull, e = ((unsigned long long)p + bytes + 15) & ~15ull;
+    if (a < lo) a = lo;
+    if (e > hi) e = hi;
+    if (e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
+// Ask L2 for what the RK update of plane z will load over the block's own
+// rows [y0, y1) x columns [x0, x1): the right-hand side and (mixed form) K,
+// D_n and, in stage 4, Q_n.  Issued a plane ahead, these take the DRAM latency
+// off the update, which runs after the plane's barrier.  Threads 0 .. jobs-1
+// issue one row of one field each.
+template <typename T>
+__device__ __forceinline__ void prefetch_update(const VArgs<T> &a, int z, int x0, int x1, int y0, int y1)
+{
+    const int rows = y1 - y0;
+    int nf = 5;
+    if constexpr (sizeof(T) == 4) nf = a.stage == 0 ? 5 : (a.stage == 1 ? 10 : 15);
+    const int t = (int)threadIdx.x;
+    if (rows <= 0 || t >= rows * nf) return;
+    const int f = t / rows, row = y0 + t % rows;
+    const int i = x0 + a.n[0] * (row + a.n[1] * z);
+    const unsigned w = (unsigned)(x1 - x0);
+    if (f < 5) {
+        bulk_prefetch(a.R[f], a.R[f] + a.np, a.R[f] + i, w * sizeof(T));
+        return;
+    }
     if constexpr (sizeof(T) == 4) {
-        if (a.stage >= 2) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) prefetch_l2(a.Kacc[k] + p);
-        }
-        if (a.stage >= 1 && a.stage <= 3) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) prefetch_l2(a.Dn[k] + p);
-        }
-        if (a.stage == 4) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) prefetch_l2(a.Qn[k] + p);
+        const int k = f % 5;
+        const bool second = f >= 10;  // second group: D_n in stages 1-3 (when K is the first), Q_n in stage 4
+        if (a.stage == 1 || (a.stage <= 3 && second)) {
+            bulk_prefetch(a.Dn[k], a.Dn[k] + a.np, a.Dn[k] + i, w * 4);
+        } else if (!second) {
+            bulk_prefetch(a.Kacc[k], a.Kacc[k] + a.np, a.Kacc[k] + i, w * 4);
+        } else {
+            bulk_prefetch(a.Qn[k], a.Qn[k] + a.np, a.Qn[k] + i, w * 8);
         }
     }
 }
 
+// Ask L2 for the primitives (W0..W4) of plane z over rows [y0, y1) x columns
+// [x0, x1), issued by threads t0 .. t0 + jobs - 1.
+template <typename T>
+__device__ __forceinline__ void prefetch_plane(const VArgs<T> &a, int z, int x0, int x1, int y0, int y1, int t0)
+{
+    const int rows = y1 - y0, t = (int)threadIdx.x - t0;
+    if (rows <= 0 || t < 0 || t >= rows * 5) return;
+    const int f = t / rows, row = y0 + t % rows;
+    const int i = x0 + a.n[0] * (row + a.n[1] * z);
+    bulk_prefetch(a.W[f], a.W[f] + a.np, a.W[f] + i, (unsigned)(x1 - x0) * sizeof(T));
+}
+
 template <typename T>
 struct Ring {
-    T *s;
+    V4<T> *s;
     int x0, y0;
-    __device__ __forceinline__ T &at(int f, int x, int y, int z) const
+    __device__ __forceinline__ const V4<T> &at(int x, int y, int z) const
     {
-        return s[((z % RING) * NPF + f) * PLANE + (y - y0 + HALO) * PX + (x - x0 + HALO)];
+        return s[(z % RING) * PLANE + (y - y0 + HALO) * PX + (x - x0 + HALO)];
     }
 };
 
@@ -154,141 +274,121 @@ struct PlaneLoad {
             }
         }
     }
-    // ask L2 for plane zz's primitives of this thread's ring nodes (the plane
-    // after the one being loaded, so its loads find them there)
-    __device__ __forceinline__ void prefetch(const VArgs<T> &a, int zz) const
-    {
-        const int zo = a.n[0] * a.n[1] * zz;
-#pragma unroll
-        for (int t = 0; t < PL_PER_THREAD; ++t) {
-            if (goff[t] >= 0) {
-                const int i = zo + goff[t];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) prefetch_l2(a.W[k] + i);
-            }
-        }
-    }
     __device__ __forceinline__ void finish(const VArgs<T> &a, const Ring<T> &rg) const
     {
 #pragma unroll
         for (int t = 0; t < PL_PER_THREAD; ++t) {
             const int idx = threadIdx.x + t * TX * TY;
             if (idx >= PLANE) continue;
-            T uu = 0, vv = 0, ww = 0, tt = 0;
+            V4<T> q{};
             if (goff[t] >= 0) {
                 const int kg = a.ga == 2 ? z : kgxy[t];
-                uu = u[t];
-                vv = v[t];
-                ww = w[t];
-                tt = node_temperature(a, kg, w0[t], w4[t]);
+                q.x = u[t];
+                q.y = v[t];
+                q.z = w[t];
+                q.w = node_temperature(a, kg, w0[t], w4[t]);
             }
-            T *p = rg.s + (size_t)(z % RING) * NPF * PLANE + idx;
-            p[0] = uu;
-            p[PLANE] = vv;
-            p[2 * PLANE] = ww;
-            p[3 * PLANE] = tt;
+            rg.s[(size_t)(z % RING) * PLANE + idx] = q;
         }
     }
 };
 
-// Second-order explicit derivatives of the primitives at one node of the
-// ring: central inside, one-sided (-3, 4, -1)/(2h) on a wall.
-// mode 0: central, 1: low wall (forward), 2: high wall (backward).  EDGE is
-// false for blocks whose nodes are all at least one node away from the x and
-// y walls, so only the z mode (uniform over a plane) is tested there.
+// Second-order explicit derivatives of (u, v, w, T) at one node of the ring:
+// central inside, one-sided (-3, 4, -1)/(2h) on a wall.  mode 0: central, 1:
+// low wall (forward), 2: high wall (backward).  EDGE is false for blocks whose
+// nodes are all at least one node away from the x and y walls, so only the z
+// mode (uniform over a plane) is tested there.
 template <typename T, bool EDGE>
 struct Stencil {
-    const T *b0, *bm1, *bp1, *bm2, *bp2;  // field-0 bases of planes j, j-1, j+1, j-2, j+2
-    int off;                              // ly * PX + lx
+    const V4<T> *b0, *bm1, *bp1, *bm2, *bp2;  // bases of planes j, j-1, j+1, j-2, j+2
+    int off;                                  // ly * PX + lx
     int xm, ym, zm;
-    T ihx, ihy, ihz;                      // 1 / (2 h)
-    __device__ __forceinline__ T val(int f) const { return b0[f * PLANE + off]; }
-    __device__ __forceinline__ T dx(int f) const
+    T ihx, ihy, ihz;                          // 1 / (2 h)
+    __device__ __forceinline__ V4<T> val() const { return b0[off]; }
+    __device__ __forceinline__ V4<T> dx() const
     {
-        const T *p = b0 + f * PLANE + off;
-        if (!EDGE || xm == 0) return (p[1] - p[-1]) * ihx;
-        if (xm == 1) return (T(-3) * p[0] + T(4) * p[1] - p[2]) * ihx;
-        return (T(3) * p[0] - T(4) * p[-1] + p[-2]) * ihx;
+        const V4<T> *p = b0 + off;
+        if (!EDGE || xm == 0) return d_central(p[1], p[-1], ihx);
+        if (xm == 1) return d_low(p[0], p[1], p[2], ihx);
+        return d_high(p[0], p[-1], p[-2], ihx);
     }
-    __device__ __forceinline__ T dy(int f) const
+    __device__ __forceinline__ V4<T> dy() const
     {
-        const T *p = b0 + f * PLANE + off;
-        if (!EDGE || ym == 0) return (p[PX] - p[-PX]) * ihy;
-        if (ym == 1) return (T(-3) * p[0] + T(4) * p[PX] - p[2 * PX]) * ihy;
-        return (T(3) * p[0] - T(4) * p[-PX] + p[-2 * PX]) * ihy;
+        const V4<T> *p = b0 + off;
+        if (!EDGE || ym == 0) return d_central(p[PX], p[-PX], ihy);
+        if (ym == 1) return d_low(p[0], p[PX], p[2 * PX], ihy);
+        return d_high(p[0], p[-PX], p[-2 * PX], ihy);
     }
-    __device__ __forceinline__ T dz(int f) const
+    __device__ __forceinline__ V4<T> dz() const
     {
-        const int o = f * PLANE + off;
-        if (zm == 0) return (bp1[o] - bm1[o]) * ihz;
-        if (zm == 1) return (T(-3) * b0[o] + T(4) * bp1[o] - bp2[o]) * ihz;
-        return (T(3) * b0[o] - T(4) * bm1[o] + bm2[o]) * ihz;
+        if (zm == 0) return d_central(bp1[off], bm1[off], ihz);
+        if (zm == 1) return d_low(b0[off], bp1[off], bp2[off], ihz);
+        return d_high(b0[off], bm1[off], bm2[off], ihz);
     }
 };
 
 __device__ __forceinline__ int wall_mode(int c, int n) { return c == 0 ? 1 : (c == n - 1 ? 2 : 0); }
 
+// Sutherland's law and Eq. reg (over mu_s), in a fixed order
 template <typename T>
 __device__ __forceinline__ void visc_coeffs(const VArgs<T> &a, T Tn, T &mu, T &mub)
 {
     if constexpr (sizeof(T) == 4)
-        mu = __fdividef(Tn * Tn * rsqrtf(Tn) * a.S1, Tn + a.S);  // Sutherland, FP32 intrinsics
+        mu = __fdividef(r_mul(r_mul(r_mul(Tn, Tn), rsqrtf(Tn)), a.S1), r_add(Tn, a.S));  // FP32 intrinsics
     else
-        mu = Tn * sqrt(Tn) * a.S1 / (Tn + a.S);  // Sutherland
-    mub = a.c0 * Tn + a.c1;                       // Eq. reg over mu_s
+        mu = r_mul(r_mul(Tn, sqrt(Tn)), a.S1) / r_add(Tn, a.S);
+    mub = r_fma(a.c0, Tn, a.c1);
 }
 
-// E_v (x) and F_v (y) at a node (Eqs. ge6, ge7, ge19, ge20, bv1, bv2);
-// the normal heat flux is zero on an adiabatic wall
-template <typename T, bool EDGE>
-__device__ __forceinline__ void flux_xy(const VArgs<T> &a, const Stencil<T, EDGE> &S, bool wantE, bool wantF, T E[4],
-                                        T F[4])
+// the three viscosity factors of the stress (Eqs. ge19, bv1-bv3) divided by Re
+template <typename T>
+struct ViscK {
+    T k43, k23, ks, mk;  // (4/3 mu + mu_b)/Re, (-2/3 mu + mu_b)/Re, mu/Re, -mu kq
+    __device__ __forceinline__ ViscK(const VArgs<T> &a, T Tn)
+    {
+        T mu, mub;
+        visc_coeffs(a, Tn, mu, mub);
+        k43 = r_mul(r_fma(T(4) / T(3), mu, mub), a.iRe);
+        k23 = r_mul(r_fma(T(-2) / T(3), mu, mub), a.iRe);
+        ks = r_mul(mu, a.iRe);
+        mk = r_mul(-mu, a.kq);
+    }
+};
+
+// Viscous fluxes at a node from its values q = (u, v, w, T) and the
+// gradients gx, gy, gz of (u, v, w, T) (Eqs. ge6-ge8, ge19, ge20, bv1-bv3).
+// The heat flux normal to an adiabatic wall is zero on the wall node (wq = 0).
+template <typename T>
+__device__ __forceinline__ V4<T> flux_E(const ViscK<T> &k, const V4<T> &q, const V4<T> &gx, const V4<T> &gy,
+                                        const V4<T> &gz, bool wq)
 {
-    const T u = S.val(0), v = S.val(1), w = S.val(2);
-    T mu, mub;
-    visc_coeffs(a, S.val(3), mu, mub);
-    const T ux = S.dx(0), vx = S.dx(1), uy = S.dy(0), vy = S.dy(1), wz = S.dz(2);
-    const T k43 = (T(4) / T(3) * mu + mub) * a.iRe, k23 = (T(-2) / T(3) * mu + mub) * a.iRe, ks = mu * a.iRe;
-    const T txy = ks * (uy + vx);
-    if (wantE) {
-        const T wx = S.dx(2), uz = S.dz(0);
-        const T txx = k43 * ux + k23 * (vy + wz);
-        const T txz = ks * (uz + wx);
-        const T qx = S.xm == 0 ? -mu * a.kq * S.dx(3) : T(0);
-        E[0] = txx;
-        E[1] = txy;
-        E[2] = txz;
-        E[3] = u * txx + v * txy + w * txz - qx;
-    }
-    if (wantF) {
-        const T wy = S.dy(2), vz = S.dz(1);
-        const T tyy = k43 * vy + k23 * (ux + wz);
-        const T tyz = ks * (vz + wy);
-        const T qy = S.ym == 0 ? -mu * a.kq * S.dy(3) : T(0);
-        F[0] = txy;
-        F[1] = tyy;
-        F[2] = tyz;
-        F[3] = u * txy + v * tyy + w * tyz - qy;
-    }
+    const T txx = r_fma(k.k43, gx.x, r_mul(k.k23, r_add(gy.y, gz.z)));
+    const T txy = r_mul(k.ks, r_add(gy.x, gx.y));
+    const T txz = r_mul(k.ks, r_add(gz.x, gx.z));
+    const T qx = wq ? r_mul(k.mk, gx.w) : T(0);
+    return V4<T>{txx, txy, txz, r_add(r_fma(q.z, txz, r_fma(q.y, txy, r_mul(q.x, txx))), -qx)};
+}
+template <typename T>
+__device__ __forceinline__ V4<T> flux_F(const ViscK<T> &k, const V4<T> &q, const V4<T> &gx, const V4<T> &gy,
+                                        const V4<T> &gz, bool wq)
+{
+    const T tyy = r_fma(k.k43, gy.y, r_mul(k.k23, r_add(gx.x, gz.z)));
+    const T txy = r_mul(k.ks, r_add(gy.x, gx.y));
+    const T tyz = r_mul(k.ks, r_add(gz.y, gy.z));
+    const T qy = wq ? r_mul(k.mk, gy.w) : T(0);
+    return V4<T>{txy, tyy, tyz, r_add(r_fma(q.z, tyz, r_fma(q.y, tyy, r_mul(q.x, txy))), -qy)};
+}
+template <typename T>
+__device__ __forceinline__ V4<T> flux_G(const ViscK<T> &k, const V4<T> &q, const V4<T> &gx, const V4<T> &gy,
+                                        const V4<T> &gz, bool wq)
+{
+    const T tzz = r_fma(k.k43, gz.z, r_mul(k.k23, r_add(gx.x, gy.y)));
+    const T txz = r_mul(k.ks, r_add(gz.x, gx.z));
+    const T tyz = r_mul(k.ks, r_add(gz.y, gy.z));
+    const T qz = wq ? r_mul(k.mk, gz.w) : T(0);
+    return V4<T>{txz, tyz, tzz, r_add(r_fma(q.z, tzz, r_fma(q.y, tyz, r_mul(q.x, txz))), -qz)};
 }
 
-// G_v (z) at a node (Eqs. ge8, ge19, ge20, bv3)
-template <typename T, bool EDGE>
-__device__ __forceinline__ void flux_z(const VArgs<T> &a, const Stencil<T, EDGE> &S, T G[4])
-{
-    const T u = S.val(0), v = S.val(1), w = S.val(2);
-    T mu, mub;
-    visc_coeffs(a, S.val(3), mu, mub);
-    const T k43 = (T(4) / T(3) * mu + mub) * a.iRe, k23 = (T(-2) / T(3) * mu + mub) * a.iRe, ks = mu * a.iRe;
-    const T tzz = k43 * S.dz(2) + k23 * (S.dx(0) + S.dy(1));
-    const T txz = ks * (S.dz(0) + S.dx(2));
-    const T tyz = ks * (S.dz(1) + S.dy(2));
-    const T qz = S.zm == 0 ? -mu * a.kq * S.dz(3) : T(0);
-    G[0] = txz;
-    G[1] = tyz;
-    G[2] = tzz;
-    G[3] = u * txz + v * tyz + w * tzz - qz;
-}
 
 // primitives of a stage state from its FP32 deviation D = (rho', m_x, m_y, m_z, E')
 __device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, int p, int kg, const float D[5])
@@ -384,19 +484,21 @@ __device__ __forceinline__ void source_and_stage(const VArgs<T> &a, int p, int k
     }
 }
 
+
 template <typename T, bool EDGE>
 __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *smraw)
 {
+    using V = V4<T>;
     constexpr int EW = TX + 2, FH = TY + 2;  // E_v row width, F_v rows (one-node halos)
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
     Ring<T> rg;
-    rg.s = reinterpret_cast<T *>(smraw);
+    rg.s = reinterpret_cast<V *>(smraw);
     rg.x0 = min(xs, max(nx - TX, 0));
     rg.y0 = min(ys, max(ny - TY, 0));
-    T *EV = rg.s + (size_t)RING * NPF * PLANE;  // [4][TY][EW], local x + 1
-    T *FV = EV + 4 * TY * EW;                   // [4][FH][TX], local y + 1
-    T *GV = FV + 4 * FH * TX;                   // [GSLOTS][4][TY][TX]
+    V *EV = rg.s + (size_t)RING * PLANE;  // [TY][EW], local x + 1
+    V *FV = EV + TY * EW;                 // [FH][TX], local y + 1
+    V *GV = FV + FH * TX;                 // [GSLOTS][TY][TX]
     const int z0 = blockIdx.z * a.zc, z1 = min(nz, z0 + a.zc);
     const int tx = (int)(threadIdx.x % TX), ty = (int)(threadIdx.x / TX);
     const int x = rg.x0 + tx, y = rg.y0 + ty;
@@ -404,6 +506,10 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     // owns all its nodes, halo nodes included, inside the box
     const bool in_dom = !EDGE || (x < nx && y < ny);
     const bool own = !EDGE || (in_dom && x >= xs && y >= ys);
+    // the block's own columns and rows (prefetch ranges) and its ring's
+    const int ox0 = xs, ox1 = min(nx, rg.x0 + TX), oy0 = ys, oy1 = min(ny, rg.y0 + TY);
+    const int rx0 = max(0, rg.x0 - HALO), rx1 = min(nx, rg.x0 + TX + HALO);
+    const int ry0 = max(0, rg.y0 - HALO), ry1 = min(ny, rg.y0 + TY + HALO);
     // G_v planes are computed in increasing order; ghi is the last one, and
     // the ring holds the GSLOTS planes up to it
     int ghi = -1000;
@@ -411,8 +517,8 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     // ring bases of planes o-3 .. o+3, refreshed once per plane (plane o + d
     // sits in slot (o + d) mod RING; o+-3 share the slots of o-+2, and a
     // stencil reaches o+-3 only next to a wall, where o-+2 lies outside the box)
-    const T *pb0, *pb1, *pb2, *pb3, *pb4, *pb5, *pb6;
-    auto pbase = [&](int k) -> const T * {  // k = d + 3, 0..6
+    const V *pb0, *pb1, *pb2, *pb3, *pb4, *pb5, *pb6;
+    auto pbase = [&](int k) -> const V * {  // k = d + 3, 0..6
         switch (k) {
         case 0: return pb0;
         case 1: return pb1;
@@ -460,7 +566,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
             auto sb = [&](int d) {
                 int t = so + d;
                 t = t >= RING ? t - RING : (t < 0 ? t + RING : t);
-                return (const T *)(rg.s + (size_t)t * NPF * PLANE);
+                return (const V *)(rg.s + (size_t)t * PLANE);
             };
             pb0 = sb(-3);
             pb1 = sb(-2);
@@ -472,37 +578,34 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         }
         // ---- 1. nodal viscous fluxes ------------------------------------------
         if (in_dom) {
-            T E[4], F[4];
-            flux_xy(a, stencil_at(tx, ty, 0, o), true, true, E, F);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                EV[(k * TY + ty) * EW + tx + 1] = E[k];
-                FV[(k * FH + ty + 1) * TX + tx] = F[k];
-            }
+            const Stencil<T, EDGE> S = stencil_at(tx, ty, 0, o);
+            const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
+            const ViscK<T> k(a, q.w);
+            EV[ty * EW + tx + 1] = flux_E(k, q, gx, gy, gz, S.xm == 0);
+            FV[(ty + 1) * TX + tx] = flux_F(k, q, gx, gy, gz, S.ym == 0);
         }
-        // halo fluxes: F_v on the y halo in warps 0-1, E_v on the x halo in
-        // warp 2, so no warp evaluates more than one halo flux per plane
+        // halo fluxes (the same arithmetic as in the tile that owns the node,
+        // so the same bits): F_v on the y halo in warps 0-1, E_v on the x halo
+        // in warp 2, so no warp evaluates more than one halo flux per plane
         if (threadIdx.x < 2 * TX) {  // F_v on the y halo
             const int t = threadIdx.x;
             const int side = t / TX, hx = t % TX;
             const int ly = side ? TY : -1;
-            const int gx = rg.x0 + hx, gy = rg.y0 + ly;
-            if (!EDGE || (gy >= 0 && gy < ny && gx < nx)) {
-                T E[4], F[4];
-                flux_xy(a, stencil_at(hx, ly, 0, o), false, true, E, F);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) FV[(k * FH + ly + 1) * TX + hx] = F[k];
+            const int gxx = rg.x0 + hx, gyy = rg.y0 + ly;
+            if (!EDGE || (gyy >= 0 && gyy < ny && gxx < nx)) {
+                const Stencil<T, EDGE> S = stencil_at(hx, ly, 0, o);
+                const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
+                FV[(ly + 1) * TX + hx] = flux_F(ViscK<T>(a, q.w), q, gx, gy, gz, S.ym == 0);
             }
         } else if (threadIdx.x < 2 * TX + 2 * TY) {  // E_v on the x halo
             const int t = threadIdx.x - 2 * TX;
             const int side = t / TY, hy = t % TY;
             const int lx = side ? TX : -1;
-            const int gx = rg.x0 + lx, gy = rg.y0 + hy;
-            if (!EDGE || (gx >= 0 && gx < nx && gy < ny)) {
-                T E[4], F[4];
-                flux_xy(a, stencil_at(lx, hy, 0, o), true, false, E, F);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) EV[(k * TY + hy) * EW + lx + 1] = E[k];
+            const int gxx = rg.x0 + lx, gyy = rg.y0 + hy;
+            if (!EDGE || (gxx >= 0 && gxx < nx && gyy < ny)) {
+                const Stencil<T, EDGE> S = stencil_at(lx, hy, 0, o);
+                const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
+                EV[hy * EW + lx + 1] = flux_E(ViscK<T>(a, q.w), q, gx, gy, gz, S.xm == 0);
             }
         }
         // G_v planes the z divergence of plane o needs: o-1 and o+1, or
@@ -515,20 +618,18 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
             const int j = o + 1, slot = j % GSLOTS;
             ghi = j;
             if (in_dom) {
-                T G[4];
-                flux_z(a, stencil_at(tx, ty, 1, j), G);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) GV[((slot * 4 + k) * TY + ty) * TX + tx] = G[k];
+                const Stencil<T, EDGE> S = stencil_at(tx, ty, 1, j);
+                const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
+                GV[(slot * TY + ty) * TX + tx] = flux_G(ViscK<T>(a, q.w), q, gx, gy, gz, S.zm == 0);
             }
         } else {
             for (int j = max(ghi + 1, jlo); j <= jlo + 2; ++j) {
                 const int slot = j % GSLOTS;
                 ghi = j;
                 if (in_dom) {
-                    T G[4];
-                    flux_z(a, stencil_at(tx, ty, j - o, j), G);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) GV[((slot * 4 + k) * TY + ty) * TX + tx] = G[k];
+                    const Stencil<T, EDGE> S = stencil_at(tx, ty, j - o, j);
+                    const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
+                    GV[(slot * TY + ty) * TX + tx] = flux_G(ViscK<T>(a, q.w), q, gx, gy, gz, S.zm == 0);
                 }
             }
         }
@@ -537,8 +638,11 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         const int zn = lhi + 1;
         const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
         if (next) pl.issue(a, zn);
-        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) pl.prefetch(a, zn + 1);  // the next issue's plane
-        if (own && o + 1 < z1) prefetch_node(a, x + nx * (y + ny * (o + 1)));
+        // L2 prefetches, one row per thread: the next update's inputs (threads
+        // 0..119 at most) and the primitives of the plane after the next load
+        // (threads 128..187 at most)
+        if (o + 1 < z1) prefetch_update(a, o + 1, ox0, ox1, oy0, oy1);
+        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) prefetch_plane(a, zn + 1, rx0, rx1, ry0, ry1, 128);
         if (own) {
             const int p = x + nx * (y + ny * o);
             T r[5];
@@ -558,40 +662,39 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
             }
             const int xm = EDGE ? wall_mode(x, nx) : 0, ym = EDGE ? wall_mode(y, ny) : 0;
             const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
-            // slots of G_v planes o-1, o+1, o, o+2, o-2 (GSLOTS = 3)
-            const int sa = (o + 2) % GSLOTS, sb = (o + 1) % GSLOTS, s0 = o % GSLOTS;
-            const int sbb = (o + 2) % GSLOTS, saa = (o + 1) % GSLOTS;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const T *e = EV + (k * TY + ty) * EW + tx + 1;
-                const T *f = FV + (k * FH + ty + 1) * TX + tx;
-                T dvx, dvy, dvz;
-                if (xm == 0)
-                    dvx = (e[1] - e[-1]) * ihx;
-                else if (xm == 1)
-                    dvx = (T(-3) * e[0] + T(4) * e[1] - e[2]) * ihx;
-                else
-                    dvx = (T(3) * e[0] - T(4) * e[-1] + e[-2]) * ihx;
-                if (ym == 0)
-                    dvy = (f[TX] - f[-TX]) * ihy;
-                else if (ym == 1)
-                    dvy = (T(-3) * f[0] + T(4) * f[TX] - f[2 * TX]) * ihy;
-                else
-                    dvy = (T(3) * f[0] - T(4) * f[-TX] + f[-2 * TX]) * ihy;
-                const int gi = (k * TY + ty) * TX + tx;
-                if (zw == 0)
-                    dvz = (GV[sb * 4 * TY * TX + gi] - GV[sa * 4 * TY * TX + gi]) * ihz;
-                else if (zw == 1)
-                    dvz = (T(-3) * GV[s0 * 4 * TY * TX + gi] + T(4) * GV[sb * 4 * TY * TX + gi] -
-                           GV[sbb * 4 * TY * TX + gi]) * ihz;
-                else
-                    dvz = (T(3) * GV[s0 * 4 * TY * TX + gi] - T(4) * GV[sa * 4 * TY * TX + gi] +
-                           GV[saa * 4 * TY * TX + gi]) * ihz;
-                r[1 + k] += dvx + dvy + dvz;
-            }
+            const V *e = EV + ty * EW + tx + 1;
+            const V *f = FV + (ty + 1) * TX + tx;
+            V dvx, dvy, dvz;
+            if (xm == 0)
+                dvx = d_central(e[1], e[-1], ihx);
+            else if (xm == 1)
+                dvx = d_low(e[0], e[1], e[2], ihx);
+            else
+                dvx = d_high(e[0], e[-1], e[-2], ihx);
+            if (ym == 0)
+                dvy = d_central(f[TX], f[-TX], ihy);
+            else if (ym == 1)
+                dvy = d_low(f[0], f[TX], f[2 * TX], ihy);
+            else
+                dvy = d_high(f[0], f[-TX], f[-2 * TX], ihy);
+            // G_v planes o-2 .. o+2 sit in slots (o + d) mod GSLOTS
+            const V *g = GV + ty * TX + tx;
+            const int sm1 = (o + 2) % GSLOTS, sp1 = (o + 1) % GSLOTS, s0 = o % GSLOTS;
+            if (zw == 0)
+                dvz = d_central(g[sp1 * TY * TX], g[sm1 * TY * TX], ihz);
+            else if (zw == 1)  // planes o, o+1, o+2
+                dvz = d_low(g[s0 * TY * TX], g[sp1 * TY * TX], g[sm1 * TY * TX], ihz);
+            else  // planes o, o-1, o-2
+                dvz = d_high(g[s0 * TY * TX], g[sm1 * TY * TX], g[sp1 * TY * TX], ihz);
+            const V dv = v_add(v_add(dvx, dvy), dvz);
+            r[1] = r_add(r[1], dv.x);
+            r[2] = r_add(r[2], dv.y);
+            r[3] = r_add(r[3], dv.z);
+            r[4] = r_add(r[4], dv.w);
             const int kg = a.ga == 0 ? x : (a.ga == 1 ? y : o);
             const bool wall = (EDGE && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) || o == 0 || o == nz - 1;
-            source_and_stage(a, p, kg, wall, w0, rg.at(a.ga, x, y, o), r, kd, dn);
+            const V qo = rg.at(x, y, o);
+            source_and_stage(a, p, kg, wall, w0, a.ga == 0 ? qo.x : (a.ga == 1 ? qo.y : qo.z), r, kd, dn);
         }
         if (next) {
             pl.finish(a, rg);
@@ -607,7 +710,7 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
 template <typename T>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) visc_rk_kernel(const VArgs<T> a)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(32) unsigned char smraw[];
     // blocks whose x and y ranges (with the one-node flux halo) stay off the
     // walls take the branch-free stencils
     const int nx = a.n[0], ny = a.n[1];

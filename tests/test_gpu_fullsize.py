@@ -7,12 +7,13 @@ hydrostatic two-temperature base) and along one horizontal axis only.  Every
 derivative across the third axis is then of a constant, which both sides
 take as zero -- exactly in the oracle and in the CUDA path's interior Thomas
 rows and explicit stencils, to FP32 rounding in the CUDA path's sub-domain end
-rows (their taps sum to zero only to rounding) and on the edge rows of the
-viscous kernel's tiles (there the two neighbouring viscous fluxes come from the
-tile and from the halo code, which may round differently) -- so on rows near
-sub-domain centres (16 or more rows from an end, where an end value's weight
-has decayed below 1e-5) and inside a tile, the 1024^3 right-hand side equals
-the oracle's on a box five nodes thick along that axis.  Both horizontal axes are covered
+rows (their taps sum to zero only to rounding) -- so on rows near sub-domain
+centres (16 or more rows from an end, where an end value's weight has decayed
+below 1e-5) the 1024^3 right-hand side equals the oracle's on a box five nodes
+thick along that axis.  The sampled rows include the first and last rows and
+columns of the viscous kernel's 32 x 8 tiles: a viscous flux next to a tile
+edge is evaluated by the tile and by its neighbour's halo code with the same
+arithmetic, so it is the same there.  Both horizontal axes are covered
 (the x sweep and the y sweep at full line length; z in both), with the
 explicit and with the compact viscous terms; the latter on 1024 x 1024 x 768,
 since its 12 scratch fields and the test's own input and output copies would
@@ -97,8 +98,9 @@ def test_rhs_1024_matches_oracle_on_sampled_rows(visc_compact, nz):
             del q
             refrow = ref[:, :, 2, :] if vary == 0 else ref[:, :, :, 2]
             errs = []
-            # rows across y: inside the viscous tiles' 8 rows; across x: inside their 32 columns
-            rows = (36, 548, 996) if vary == 0 else (48, 560, 976)
+            # rows across y (viscous tiles of 8 rows: 40 and 47 are a tile's first
+            # and last) and columns across x (tiles of 32: 32 and 543 are edges)
+            rows = (36, 40, 47, 548, 996) if vary == 0 else (32, 48, 543, 560, 976)
             for row in rows:
                 got = (r[:, :, row, :] if vary == 0 else r[:, :, :, row]).cpu().numpy().astype(np.float64)
                 errs.append(field_rel(got, refrow))

@@ -164,64 +164,31 @@ __device__ __forceinline__ V d_high(const V &p0, const V &pm1, const V &pm2, T i
     return v_mul(v_add(v_fma(pm1, T(-4), v_mul(p0, T(3))), pm2), ih);
 }
 
-// ---- L2 prefetch ---------------------------------------------------------------
-// One bulk prefetch of the bytes [p, p + bytes) of a field that spans
-// [f0, f1), clipped to 16-byte boundaries inside the field (a bulk prefetch
-// takes 16-byte aligned addresses and sizes).  One thread asks for a whole
-// tile row this way, instead of every thread issuing a prefetch per value.
-__device__ __forceinline__ void bulk_prefetch(const void *f0, const void *f1, const void *p, unsigned bytes)
-{
-    const unsigned long long lo = ((unsigned long long)f0 + 15) & ~15ull, hi = (unsigned long long)f1 & ~15ull;
-    unsigned long long a = (unsigned long long)p & ~15ull, e = ((unsigned long long)p + bytes + 15) & ~15ull;
-    if (a < lo) a = lo;
-    if (e > hi) e = hi;
-    if (e > a)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
-}
-
-// Ask L2 for what the RK update of plane z will load over the block's own
-// rows [y0, y1) x columns [x0, x1): the right-hand side and (mixed form) K,
-// D_n and, in stage 4, Q_n.  Issued a plane ahead, these take the DRAM latency
-// off the update, which runs after the plane's barrier.  Threads 0 .. jobs-1
-// issue one row of one field each.
+// Ask L2 for what the RK update of node p will load: its right-hand side and
+// (mixed form) K, D_n and, in stage 4, Q_n.  Issued a plane ahead, these take
+// the DRAM latency off the update, which runs after the plane's barrier; an L2
+// prefetch holds no register.  (One bulk prefetch per tile row and field
+// instead, from a few threads, was 18% slower for the whole kernel.)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 template <typename T>
-__device__ __forceinline__ void prefetch_update(const VArgs<T> &a, int z, int x0, int x1, int y0, int y1)
+__device__ __forceinline__ void prefetch_node(const VArgs<T> &a, int p)
 {
-    const int rows = y1 - y0;
-    int nf = 5;
-    if constexpr (sizeof(T) == 4) nf = a.stage == 0 ? 5 : (a.stage == 1 ? 10 : 15);
-    const int t = (int)threadIdx.x;
-    if (rows <= 0 || t >= rows * nf) return;
-    const int f = t / rows, row = y0 + t % rows;
-    const int i = x0 + a.n[0] * (row + a.n[1] * z);
-    const unsigned w = (unsigned)(x1 - x0);
-    if (f < 5) {
-        bulk_prefetch(a.R[f], a.R[f] + a.np, a.R[f] + i, w * sizeof(T));
-        return;
-    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) prefetch_l2(a.R[k] + p);
     if constexpr (sizeof(T) == 4) {
-        const int k = f % 5;
-        const bool second = f >= 10;  // second group: D_n in stages 1-3 (when K is the first), Q_n in stage 4
-        if (a.stage == 1 || (a.stage <= 3 && second)) {
-            bulk_prefetch(a.Dn[k], a.Dn[k] + a.np, a.Dn[k] + i, w * 4);
-        } else if (!second) {
-            bulk_prefetch(a.Kacc[k], a.Kacc[k] + a.np, a.Kacc[k] + i, w * 4);
-        } else {
-            bulk_prefetch(a.Qn[k], a.Qn[k] + a.np, a.Qn[k] + i, w * 8);
+        if (a.stage >= 2) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) prefetch_l2(a.Kacc[k] + p);
+        }
+        if (a.stage >= 1 && a.stage <= 3) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) prefetch_l2(a.Dn[k] + p);
+        }
+        if (a.stage == 4) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) prefetch_l2(a.Qn[k] + p);
         }
     }
-}
-
-// Ask L2 for the primitives (W0..W4) of plane z over rows [y0, y1) x columns
-// [x0, x1), issued by threads t0 .. t0 + jobs - 1.
-template <typename T>
-__device__ __forceinline__ void prefetch_plane(const VArgs<T> &a, int z, int x0, int x1, int y0, int y1, int t0)
-{
-    const int rows = y1 - y0, t = (int)threadIdx.x - t0;
-    if (rows <= 0 || t < 0 || t >= rows * 5) return;
-    const int f = t / rows, row = y0 + t % rows;
-    const int i = x0 + a.n[0] * (row + a.n[1] * z);
-    bulk_prefetch(a.W[f], a.W[f] + a.np, a.W[f] + i, (unsigned)(x1 - x0) * sizeof(T));
 }
 
 template <typename T>
@@ -271,6 +238,20 @@ struct PlaneLoad {
                 v[t] = a.W[2][i];
                 w[t] = a.W[3][i];
                 w4[t] = a.W[4][i];
+            }
+        }
+    }
+    // ask L2 for plane zz's primitives of this thread's ring nodes (the plane
+    // after the one being loaded, so its loads find them there)
+    __device__ __forceinline__ void prefetch(const VArgs<T> &a, int zz) const
+    {
+        const int zo = a.n[0] * a.n[1] * zz;
+#pragma unroll
+        for (int t = 0; t < PL_PER_THREAD; ++t) {
+            if (goff[t] >= 0) {
+                const int i = zo + goff[t];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) prefetch_l2(a.W[k] + i);
             }
         }
     }
@@ -506,10 +487,6 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
     // owns all its nodes, halo nodes included, inside the box
     const bool in_dom = !EDGE || (x < nx && y < ny);
     const bool own = !EDGE || (in_dom && x >= xs && y >= ys);
-    // the block's own columns and rows (prefetch ranges) and its ring's
-    const int ox0 = xs, ox1 = min(nx, rg.x0 + TX), oy0 = ys, oy1 = min(ny, rg.y0 + TY);
-    const int rx0 = max(0, rg.x0 - HALO), rx1 = min(nx, rg.x0 + TX + HALO);
-    const int ry0 = max(0, rg.y0 - HALO), ry1 = min(ny, rg.y0 + TY + HALO);
     // G_v planes are computed in increasing order; ghi is the last one, and
     // the ring holds the GSLOTS planes up to it
     int ghi = -1000;
@@ -638,11 +615,8 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, unsigned char *s
         const int zn = lhi + 1;
         const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
         if (next) pl.issue(a, zn);
-        // L2 prefetches, one row per thread: the next update's inputs (threads
-        // 0..119 at most) and the primitives of the plane after the next load
-        // (threads 128..187 at most)
-        if (o + 1 < z1) prefetch_update(a, o + 1, ox0, ox1, oy0, oy1);
-        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) prefetch_plane(a, zn + 1, rx0, rx1, ry0, ry1, 128);
+        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) pl.prefetch(a, zn + 1);  // the next issue's plane
+        if (own && o + 1 < z1) prefetch_node(a, x + nx * (y + ny * (o + 1)));
         if (own) {
             const int p = x + nx * (y + ny * o);
             T r[5];

@@ -336,6 +336,55 @@ nopcs_status nopcs_operator_apply(int N, int sub_n, int kind, double alpha_f, do
 nopcs_status nopcs_band_apply(int N, int kind, double alpha_f, double thresh, const double *f, double *g,
                               int *half_width, int *interior_lo, int *interior_hi);
 
+/*
+ * ---- One box split into z-slabs across ranks (Sec. 3; the rank grid of Sec. 4)
+ *
+ * A rank that owns the planes [z0, z1) of a box -- whole NOHAP sub-domains of
+ * the z lines -- computes the derivative of its planes from them plus the
+ * halo planes [lo, z0) and [z1, hi) that the sub-domain end rows (rows of the
+ * global C = A^-1 B, Eqs. CS:fpCf, CS:fpCf_i, reaching n_b = 48 points in FP64
+ * and 24 in FP32) and the interior stencil reach.  The caller receives those
+ * halo planes from the neighbouring ranks into its own memory (e.g. NCCL
+ * send/recv; no remote loads); the result on [z0, z1) is then that of the
+ * single-domain solve of the whole box, bit for bit.  A slab holds operator
+ * tables only (a few KB), no field.
+ *
+ * nopcs_slab_create: `box` is the whole box (its n, len and sub_n are used;
+ * sub_n must be 0 or >= 3, no tuning); z0 and z1 must be sub-domain
+ * boundaries of the z partition.  Tables go to the current device.  Errors:
+ * EINVAL (sizes, unaligned slab), ENOMEM, ECUDA.  On error *out is NULL and
+ * nopcs_slab_last_error(NULL) has the message.
+ */
+typedef struct nopcs_slab nopcs_slab; /* opaque, library-owned */
+nopcs_status nopcs_slab_create(const nopcs_box_desc *box, int z0, int z1, nopcs_slab **out);
+void nopcs_slab_destroy(nopcs_slab *slab);
+const char *nopcs_slab_last_error(const nopcs_slab *slab);
+
+/* Planes [*lo, *hi) of the box that a slab's local field of `dtype` (0 f64,
+ * 1 f32) holds: own planes plus halo, lo <= z0 < z1 <= hi. */
+nopcs_status nopcs_slab_extent(const nopcs_slab *slab, int dtype, int *lo, int *hi);
+
+/*
+ * NOHAP first derivative along `axis` of a slab's field: f (device) holds the
+ * planes [lo, hi) of nopcs_slab_extent (nx*ny values each, x fastest), the
+ * halo planes already received; df (device) receives the own planes [z0, z1)
+ * only, nx*ny*(z1 - z0) values.  Along x and y only the own planes of f are
+ * read.  FP64 (dtype 0) or FP32 (dtype 1) as nopcs_derivative order 1,
+ * Thomas form.  Enqueued on `stream`; no wait.  Must be called with the
+ * slab's device current.  Errors: EINVAL, ECUDA.
+ */
+nopcs_status nopcs_slab_derivative(nopcs_slab *slab, int axis, int dtype, const void *f, void *df, void *stream);
+
+/*
+ * Host FP64 evaluation of the same restricted line operator, for inspection
+ * and tests (needs no GPU): a line of N points with sub-domains of sub_n and
+ * end-row taps truncated at `thresh`; f holds points [*lo, *hi) (set on
+ * return; pass f = g = NULL to query them only), g receives points
+ * [z0, z1), dimensionless (times h).  Errors: EINVAL.
+ */
+nopcs_status nopcs_slab_line_apply(int N, int sub_n, double thresh, int z0, int z1, const double *f, double *g,
+                                   int *lo, int *hi);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,16 @@ _L.nopcs_operator_rows.argtypes = [_i, _i, _i, _d, _d, C.POINTER(_i), C.POINTER(
 _L.nopcs_operator_apply.argtypes = [_i, _i, _i, _d, _d, C.c_void_p, C.c_void_p]
 _L.nopcs_plane_fields.argtypes = [_vp, _i, _i, _i, _i, _vp]
 _L.nopcs_band_apply.argtypes = [_i, _i, _d, _d, C.c_void_p, C.c_void_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]
+_L.nopcs_slab_create.argtypes = [C.POINTER(nopcs_box_desc), _i, _i, C.POINTER(_vp)]
+_L.nopcs_slab_destroy.argtypes = [_vp]
+_L.nopcs_slab_destroy.restype = None
+_L.nopcs_slab_last_error.argtypes = [_vp]
+_L.nopcs_slab_last_error.restype = C.c_char_p
+_L.nopcs_slab_extent.argtypes = [_vp, _i, C.POINTER(_i), C.POINTER(_i)]
+_L.nopcs_slab_derivative.argtypes = [_vp, _i, _i, _vp, _vp, _vp]
+_L.nopcs_slab_line_apply.argtypes = [_i, _i, _d, _i, _i, C.c_void_p, C.c_void_p, C.POINTER(_i), C.POINTER(_i)]
+for _name in ("nopcs_slab_create", "nopcs_slab_extent", "nopcs_slab_derivative", "nopcs_slab_line_apply"):
+    getattr(_L, _name).restype = _i
 for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_plane_fields", "nopcs_init", "nopcs_set_state",
               "nopcs_get_state", "nopcs_reset_state", "nopcs_set_step", "nopcs_set_memory_limit", "nopcs_derivative",
               "nopcs_derivative2_noalloc",
@@ -261,3 +271,57 @@ def nopcs_operator_apply(N: int, sub_n: int, f, kind: int = 0, alpha_f: float = 
     if st != NOPCS_OK:
         raise NopcsError(st, "bad operator request")
     return g
+
+
+def _slab_check(slab, st):
+    if st != NOPCS_OK:
+        msg = _L.nopcs_slab_last_error(slab)
+        raise NopcsError(st, msg.decode() if msg else "")
+
+
+def nopcs_slab_create(box, z0: int, z1: int):
+    """A z-slab [z0, z1) of the box (dict or nopcs_box_desc); returns a handle."""
+    d = box if isinstance(box, nopcs_box_desc) else box_desc(box)
+    out = _vp()
+    _slab_check(None, _L.nopcs_slab_create(C.byref(d), z0, z1, C.byref(out)))
+    return out.value
+
+
+def nopcs_slab_destroy(slab) -> None:
+    _L.nopcs_slab_destroy(slab)
+
+
+def nopcs_slab_extent(slab, dtype: int):
+    lo, hi = _i(), _i()
+    _slab_check(slab, _L.nopcs_slab_extent(slab, dtype, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def nopcs_slab_derivative(slab, axis: int, dtype: int, f_ptr: int, df_ptr: int, stream: int = 0) -> None:
+    _slab_check(slab, _L.nopcs_slab_derivative(slab, axis, dtype, f_ptr, df_ptr, _vp(stream or None)))
+
+
+def nopcs_slab_line_apply(N: int, sub_n: int, thresh: float, z0: int, z1: int, f=None):
+    """Host FP64 evaluation of the slab-restricted line operator: with f = None
+    returns (lo, hi); else f holds points [lo, hi) and the result (points
+    [z0, z1), times h) is returned."""
+    import numpy as np
+    lo, hi = _i(), _i()
+    if f is None:
+        st = _L.nopcs_slab_line_apply(N, sub_n, thresh, z0, z1, None, None, C.byref(lo), C.byref(hi))
+        if st != NOPCS_OK:
+            raise NopcsError(st, "bad slab request")
+        return lo.value, hi.value
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.zeros(z1 - z0)
+    st = _L.nopcs_slab_line_apply(N, sub_n, thresh, z0, z1, f.ctypes.data, g.ctypes.data, C.byref(lo),
+                                  C.byref(hi))
+    if st != NOPCS_OK:
+        raise NopcsError(st, "bad slab request")
+    return g
+
+
+
+def nopcs_slab_last_error(slab) -> str:
+    m = _L.nopcs_slab_last_error(slab)
+    return m.decode() if m else ""

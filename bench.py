@@ -67,7 +67,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-n", type=int, default=128, help="oracle sample grid for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle sample steps for the CPU baseline")
+    ap.add_argument("--cpu1-n", type=int, default=64, help="oracle sample grid for the one-core timing")
+    ap.add_argument("--cpu1-steps", type=int, default=4, help="oracle sample steps for the one-core timing")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the short derivative-microbenchmark and 64-box runs of the default line")
     ap.add_argument("--workload", default="rk", choices=["rk", "deriv", "batched"],
                     help="rk: the RK-step benchmark (default); deriv: the derivative microbenchmark; "
                          "batched: 64 uneven boxes in one context")
@@ -148,20 +152,28 @@ def box(n, sub_n, **kw):
     return S.box_params((n, n, n), sub_n=(sub_n,) * 3, **kw)
 
 
-def run_cpu_oracle(n, steps, warmup=0):
-    """Time the FP64 oracle as it stands (OpenMP, all host cores)."""
+def run_cpu_oracle(n, steps, warmup=0, threads=None):
+    """Time the FP64 oracle as it stands (OpenMP over lines; all host cores,
+    or `threads` of them)."""
     import oracle
     p = box(n, min(64, n))
     p["base_subtract"] = 1
-    s = oracle.Solver(p)
-    Q = s.initial_state()
-    if warmup:
-        Q = s.step(Q, warmup)
-    t0 = time.perf_counter()
-    Q = s.step(Q, steps)
-    dt = time.perf_counter() - t0
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
+    try:
+        s = oracle.Solver(p)
+        Q = s.initial_state()
+        if warmup:
+            Q = s.step(Q, warmup)
+        t0 = time.perf_counter()
+        Q = s.step(Q, steps)
+        dt = time.perf_counter() - t0
+        used = oracle.num_threads()
+    finally:
+        oracle.set_num_threads(all_threads)
     pts = float(n) ** 3 * 4 * steps
-    return pts / dt, dt, oracle.num_threads()
+    return pts / dt, dt, used
 
 
 def workload_name(n, sub_n):
@@ -181,7 +193,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(args.n, args.sub_n), "grid": [args.n] * 3, "sub_n": args.sub_n,
+            "config": {"workload": "FP64 CPU oracle on %d host cores, timed on a bounded sample (a %d^3 box, "
+                                   "base-subtracted, sub-domains of %d) of the workload: %s"
+                                   % (cores, n, min(64, n), workload_name(args.n, args.sub_n)),
+                       "grid": [args.n] * 3, "sub_n": args.sub_n,
                        "precision": "fp64 (the oracle)", "sample_grid": [n] * 3,
                        "parallelism": "rank 0 only (host cores)"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
@@ -190,19 +205,15 @@ def run_reference(args):
     return 0
 
 
-def run_deriv_microbench(args):
+def deriv_rows(N, steps, warmup):
     """NOHAP first derivative of a seeded 512^3 field (random-phase sines plus
     N(0, 1e-3^2) noise) along x, y, z: Thomas form in FP64 and FP32 and the
     3xTF32 and BF16x3 tensor-core forms, sub-domains of 32, 64 and 128, and the banded
     explicit form (FP32, no sub-domains).  Each case is timed
     with CUDA events over `steps` calls after `warmup`; the field (0.5-1 GB) is
-    larger than L2."""
+    larger than L2.  Returns (rows, peaks)."""
     import torch
     import nopcs_synth as S
-    from paper_2203_00879_gb300 import build as B
-    B.build()
-    from paper_2203_00879_gb300 import nopcs as N
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     n = 512
     hbm, peak_kind = peaks()
     try:
@@ -236,16 +247,16 @@ def run_deriv_microbench(args):
             for dname, dt, f in cases:
                 out = torch.empty_like(f)
                 for axis in range(3):
-                    for _ in range(args.warmup):
+                    for _ in range(warmup):
                         N.nopcs_derivative(ctx, 0, axis, 1, dt, f.data_ptr(), out.data_ptr(), st.cuda_stream)
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     torch.cuda.synchronize()
                     e0.record(st)
-                    for _ in range(args.steps):
+                    for _ in range(steps):
                         N.nopcs_derivative(ctx, 0, axis, 1, dt, f.data_ptr(), out.data_ptr(), st.cuda_stream)
                     e1.record(st)
                     N.nopcs_synchronize(ctx)
-                    ms = e0.elapsed_time(e1) / args.steps
+                    ms = e0.elapsed_time(e1) / steps
                     es = 8 if dt == 0 else 4
                     gbs = 2 * es * n ** 3 / (ms * 1e-3) / 1e9
                     row = {"form": form_name, "dtype": dname, "sub_n": sub_n, "axis": "xyz"[axis], "ms": ms,
@@ -266,6 +277,44 @@ def run_deriv_microbench(args):
                         row.update({"tensor_tflops": tflops, "tensor_frac": tflops / bf16_peak})
                     rows.append(row)
             N.nopcs_destroy(ctx)
+    del f64, f32, px, py, pz
+    torch.cuda.empty_cache()
+    return rows, {"hbm": hbm, "peak_kind": peak_kind, "tf32_peak": tf32_peak, "tf32_kind": tf32_kind,
+                  "bf16_peak": bf16_peak}
+
+
+def deriv_summary(rows):
+    """Best case per form and dtype (fastest over sub-domain lengths and axes,
+    and the slowest axis of that sub-domain length)."""
+    out = {}
+    for r in rows:
+        if "ms" not in r:
+            continue
+        key = r["form"] + "_" + r["dtype"]
+        same = [q for q in rows if q.get("form") == r["form"] and q.get("dtype") == r["dtype"]
+                and q.get("sub_n") == r.get("sub_n") and "ms" in q]
+        worst = max(q["ms"] for q in same)
+        cur = out.get(key)
+        if cur is None or worst < cur["ms_slowest_axis"]:
+            ent = {"sub_n": r.get("sub_n"), "ms_slowest_axis": worst,
+                   "ms_per_axis": {q["axis"]: round(q["ms"], 4) for q in same},
+                   "hbm_frac_slowest_axis": min(q["hbm_frac"] for q in same)}
+            if "tensor_frac" in r:
+                ent["tensor_frac_slowest_axis"] = min(q["tensor_frac"] for q in same)
+            out[key] = ent
+    return out
+
+
+def run_deriv_microbench(args):
+    import torch
+    from paper_2203_00879_gb300 import build as B
+    B.build()
+    from paper_2203_00879_gb300 import nopcs as N
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = 512
+    rows, pk = deriv_rows(N, args.steps, args.warmup)
+    hbm, peak_kind, tf32_peak, tf32_kind, bf16_peak = (pk["hbm"], pk["peak_kind"], pk["tf32_peak"], pk["tf32_kind"],
+                                                       pk["bf16_peak"])
     best = max((r for r in rows if r.get("dtype") == "f32"), key=lambda r: r["points_per_s"])
     line = {"metric": "NOHAP first-derivative points/s at 512^3 (microbenchmark)", "value": best["points_per_s"],
             "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -276,22 +325,19 @@ def run_deriv_microbench(args):
             "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s", "peak_kind": peak_kind,
                          "tensor_peak_tflops": tf32_peak, "tensor_peak_kind": tf32_kind,
                          "bf16_peak_tflops": bf16_peak},
+            "summary": deriv_summary(rows),
             "cases": rows}
     print(json.dumps(line))
     return 0
 
 
-def run_batched(args):
+def batched_run(N, steps, warmup):
     """64 independent boxes (edges from {32, 48, 64, 96, 128}, heights 1-2x,
     temperature contrasts 50-250 K), mixed precision, sub-domain lengths chosen
     by the autotuner, advanced together: every RK step is one CUDA-graph launch
-    whose branches are the boxes."""
+    whose branches are the boxes.  Returns (points, ms, init_s, tuned)."""
     import torch
     import nopcs_synth as S
-    from paper_2203_00879_gb300 import build as B
-    B.build()
-    from paper_2203_00879_gb300 import nopcs as N
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     boxes = S.uneven_boxes(64, seed=11)
     for b in boxes:
         b["sub_n"] = (-1, -1, -1)
@@ -300,11 +346,11 @@ def run_batched(args):
     ctx = N.nopcs_init(boxes, prec=N.NOPCS_MIXED, stream=st.cuda_stream)
     init_s = time.perf_counter() - t0
     npts = sum(b["n"][0] * b["n"][1] * b["n"][2] for b in boxes)
-    N.nopcs_rk_step(ctx, args.warmup)
+    N.nopcs_rk_step(ctx, warmup)
     N.nopcs_synchronize(ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    N.nopcs_rk_step(ctx, args.steps)
+    N.nopcs_rk_step(ctx, steps)
     e1.record(st)
     N.nopcs_synchronize(ctx)
     ms = e0.elapsed_time(e1)
@@ -313,6 +359,16 @@ def run_batched(args):
         k = str(N.nopcs_box_info(ctx, i)["sub_n"])
         tuned[k] = tuned.get(k, 0) + 1
     N.nopcs_destroy(ctx)
+    return npts, ms, init_s, tuned
+
+
+def run_batched(args):
+    import torch
+    from paper_2203_00879_gb300 import build as B
+    B.build()
+    from paper_2203_00879_gb300 import nopcs as N
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    npts, ms, init_s, tuned = batched_run(N, args.steps, args.warmup)
     line = {"metric": "RK-stage grid-point updates/s, 64 uneven boxes batched (mixed)",
             "value": npts * 4 * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -379,8 +435,12 @@ def main():
     tile_lines = N.nopcs_box_info(ctx, 0)["tile_lines"]
     N.nopcs_rk_step(ctx, W)
     N.nopcs_synchronize(ctx)
-    N.nopcs_set_profiling(ctx, True)
-    N.nopcs_profile_read(ctx, reset=True)
+    # Place the timed window on the filter's every-50-steps cadence so that it
+    # holds ceil(K / 50) filters (the count a long run amortises to, rounded
+    # up): the first timed step ends on a multiple of 50.
+    N.nopcs_set_step(ctx, 0, 49)
+    filters_in_window = (K + 49) // 50
+    # ---- timed region: graph replay, as nopcs_rk_step runs in production ----
     clocks = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -394,17 +454,32 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    prof = N.nopcs_profile_read(ctx, reset=True)
-    N.nopcs_set_profiling(ctx, False)
     ms_max = rank_max(ms)
     value = job_rate(npts, 4, K, world, ms_max)
+
+    # ---- per-kernel times: a separate window of direct launches, each kernel
+    # between CUDA events on the context stream (same kernels, same state) ----
+    KP = 3
+    N.nopcs_set_profiling(ctx, True)
+    N.nopcs_profile_read(ctx, reset=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    N.nopcs_rk_step(ctx, KP)
+    e1.record(stream)
+    barrier()
+    ms_prof = e0.elapsed_time(e1)
+    prof = N.nopcs_profile_read(ctx, reset=True)
+    N.nopcs_set_profiling(ctx, False)
     launches_per_kind = {"prep": 1, "sweep_x": 1, "sweep_y": 1, "sweep_z": 1, "visc_rk_update": 1,
                          "wall_bc": 3, "filter": 4, "diagnostics": 2}
-    gpu_launches = int(sum(v[1] * launches_per_kind.get(k, 1) for k, v in prof.items()))
+    step_launches = sum(v[1] * launches_per_kind.get(k, 1) for k, v in prof.items()
+                        if k not in ("filter", "diagnostics")) / KP
+    gpu_launches = int(round(step_launches * K)) + 4 * filters_in_window + 2
 
     # dominant kernel against the HBM roofline
     hbm, peak_kind = peaks()
-    dom = max((k for k in prof if k in ALG_BYTES_MIXED), key=lambda k: prof[k][0])
+    dom = max((k for k in prof if k in ALG_BYTES_MIXED and k != "filter"), key=lambda k: prof[k][0])
     avg_ms = prof[dom][0] / max(prof[dom][1], 1)
     alg = ALG_BYTES_MIXED[dom] * npts
     achieved = alg / (avg_ms * 1e-3) / 1e9
@@ -418,8 +493,20 @@ def main():
             traffic = ent["bytes_per_point"] * npts
     except Exception:
         traffic = None
-    per_kernel = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(ms, 1e-9)} for k, v in prof.items()
-                  if v[1]}
+    per_kernel = {}
+    for k, v in prof.items():
+        if not v[1]:
+            continue
+        ent = {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / v[1], "share": v[0] / max(ms_prof, 1e-9)}
+        if k in ALG_BYTES_MIXED and k != "filter":
+            gbs = ALG_BYTES_MIXED[k] * npts / (v[0] / v[1] * 1e-3) / 1e9
+            ent.update(alg_bytes_per_point=ALG_BYTES_MIXED[k], achieved_gbs=gbs, frac=gbs / hbm)
+        per_kernel[k] = ent
+    # the whole RK stage against the algorithmic 160 B per point and stage
+    # (FP64 state, three-register classical RK4)
+    whole = 160.0 * npts * 4 * K / (ms * 1e-3) / 1e9
+    whole_step = {"alg_bytes_per_point_stage": 160, "achieved_gbs": whole, "frac": whole / hbm,
+                  "peak_kind": peak_kind}
     N.nopcs_destroy(ctx)
     torch.cuda.synchronize()
 
@@ -449,7 +536,8 @@ def main():
         barrier()
         el = rank_max(time.perf_counter() - t0)
         e2e = {"value": world * npts * 4 * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": 10 * 8, "pinned_host": pinned, "steps": args.e2e_steps}
+               "d2h_bytes_per_step": 10 * 8, "pinned_host": pinned, "steps": args.e2e_steps,
+               "readback": "the diagnostics (10 doubles) every step; the state stays on the device"}
         del host
         N.nopcs_destroy(ctx)
         torch.cuda.synchronize()
@@ -466,18 +554,18 @@ def main():
             p64 = box(n64, args.sub_n, seed=1 + rank)
             ctx = N.nopcs_init([p64], prec=N.NOPCS_FP64, stream=st)
         N.nopcs_rk_step(ctx, 1)
-        N.nopcs_set_profiling(ctx, True)
-        N.nopcs_profile_read(ctx, reset=True)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        profiler_range(True)
         e0.record(stream)
         N.nopcs_rk_step(ctx, args.fp64_steps)
         e1.record(stream)
-        profiler_range(False)
         barrier()
         m64 = rank_max(e0.elapsed_time(e1))
+        N.nopcs_set_profiling(ctx, True)
+        N.nopcs_profile_read(ctx, reset=True)
+        N.nopcs_rk_step(ctx, 1)
         p64k = N.nopcs_profile_read(ctx, reset=True)
+        N.nopcs_set_profiling(ctx, False)
         v64 = world * float(n64) ** 3 * 4 * args.fp64_steps / (m64 * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "grid": [n64] * 3, "steps": args.fp64_steps,
                 "ms_per_step": m64 / args.fp64_steps, "mixed_over_fp64": value / v64,
@@ -491,18 +579,18 @@ def main():
         pc = box(nc, args.sub_n, seed=1 + rank, visc_compact=1)
         ctx = N.nopcs_init([pc], prec=N.NOPCS_MIXED, stream=st)
         N.nopcs_rk_step(ctx, 1)
-        N.nopcs_set_profiling(ctx, True)
-        N.nopcs_profile_read(ctx, reset=True)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        profiler_range(True)
         e0.record(stream)
         N.nopcs_rk_step(ctx, args.compact_steps)
         e1.record(stream)
-        profiler_range(False)
         barrier()
         mc = rank_max(e0.elapsed_time(e1))
+        N.nopcs_set_profiling(ctx, True)
+        N.nopcs_profile_read(ctx, reset=True)
+        N.nopcs_rk_step(ctx, 1)
         pr = N.nopcs_profile_read(ctx, reset=True)
+        N.nopcs_set_profiling(ctx, False)
         N.nopcs_destroy(ctx)
         ptc = float(nc) ** 3
         kc = {}
@@ -518,12 +606,31 @@ def main():
                    "steps": args.compact_steps, "ms_per_step": mc / args.compact_steps, "kernels": kc,
                    "explicit_over_compact": value / (world * ptc * 4 * args.compact_steps / (mc * 1e-3))}
 
+    # the derivative microbenchmark (512^3) and the 64-box batched workload,
+    # in short runs: best case per form, and the batched rate
+    deriv = None
+    batched = None
+    if args.extra:
+        torch.cuda.empty_cache()
+        rows, pk = deriv_rows(N, 10, 3)
+        deriv = {"grid": [512] * 3, "metric": "NOHAP first derivative of one field, ms per call", "steps": 10,
+                 "hbm_peak_gbs": pk["hbm"], "tf32_peak_tflops": pk["tf32_peak"],
+                 "bf16_peak_tflops": pk["bf16_peak"], "best": deriv_summary(rows)}
+        bn, bms, binit, btuned = batched_run(N, 20, 3)
+        batched = {"value": world * bn * 4 * 20 / (bms * 1e-3), "unit": UNIT, "points": bn, "steps": 20,
+                   "ms_per_step": bms / 20, "init_s": binit, "tuned_sub_n": btuned,
+                   "workload": "64 uneven two-temperature boxes, edges 32-128, heights 1-2x edge, dT 50-250 K, "
+                               "seed 11; one CUDA graph per step, one branch per box"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, dt, cores = run_cpu_oracle(args.cpu_n, args.cpu_steps)
+        rate1, dt1, cores1 = run_cpu_oracle(args.cpu1_n, args.cpu1_steps, threads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "FP64 CPU oracle, %d RK4 steps of a %d^3 box of the same physics (base-subtracted), "
-                         "%.1f s" % (args.cpu_steps, args.cpu_n, dt)}
+                         "%.1f s" % (args.cpu_steps, args.cpu_n, dt),
+               "one_core": {"value": rate1, "unit": UNIT, "cores": cores1,
+                            "sample": "%d RK4 steps of a %d^3 box, %.1f s" % (args.cpu1_steps, args.cpu1_n, dt1)}}
 
     if rank == 0:
         line = {
@@ -532,17 +639,22 @@ def main():
             "dtype": "f32/f64", "data": "synthetic",
             "config": {"workload": workload_name(n, args.sub_n),
                        "grid": [n, n, n], "sub_n": args.sub_n, "precision": "mixed", "form": "thomas",
-                       "sweep_tile_lines": tile_lines,
+                       "sweep_tile_lines": tile_lines, "launch": "CUDA graph replay, one graph per RK4 step",
+                       "filters_in_window": filters_in_window,
                        "l2": "inputs larger than L2 (FP64 state %.1f GB)" % (40 * npts / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                         "alg_bytes_per_point": ALG_BYTES_MIXED[dom], "avg_launch_ms": avg_ms},
+                         "alg_bytes_per_point": ALG_BYTES_MIXED[dom], "avg_launch_ms": avg_ms,
+                         "timing": "CUDA events around each launch, %d-step window of direct launches" % KP},
+            "whole_step": whole_step,
             "kernels": per_kernel,
             "gpu_launches": gpu_launches,
             "e2e": e2e,
             "fp64_form": fp64,
             "compact_viscous_form": compact,
+            "deriv_microbench": deriv,
+            "batched_64_boxes": batched,
             "cpu_baseline": cpu,
             "clocks": clk,
             "diagnostics": {"step": diag["step"], "max_speed": diag["max_speed"], "max_dp": diag["max_dp"]},

@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nopcs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_FMA = os.path.join(_HERE, "liboracle_fma.so")
 
 OUCS3 = (0.3793894912, 0.7877868952, 0.045801298, -0.025)  # alpha, b1, b2, beta
 DERIV, FILTER, D2 = 0, 1, 2
@@ -25,14 +26,25 @@ LELE_D2 = (2.0 / 11.0, 12.0 / 11.0, 3.0 / 11.0)  # alpha, a, b of the sixth-orde
 THRESH_FP64 = 1e-16
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (gcc, -O2, OpenMP) next to its source."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp,
+def build(force: bool = False, contracted: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, OpenMP) next to its source.  contracted:
+    the same source with multiply-adds fused into FMAs wherever the compiler
+    likes (-ffp-contract=fast; FMA instructions are native on aarch64), a
+    second rounding of the same arithmetic, used only to size round-off
+    differences."""
+    path = _LIB_FMA if contracted else _LIB
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + ".tmp%d" % os.getpid()
+        extra = []
+        if contracted:
+            extra = ["-ffp-contract=fast"]
+            import platform
+            if platform.machine() in ("x86_64", "AMD64"):
+                extra.append("-mfma")
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", *extra, "-o", tmp,
                                _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, path)
+    return path
 
 
 class _Box(C.Structure):
@@ -46,6 +58,7 @@ class _Box(C.Structure):
 
 
 _lib = None
+_lib_fma = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
@@ -53,7 +66,20 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        _lib = _bind(C.CDLL(build()))
+    return _lib
+
+
+def lib_contracted():
+    """The oracle built with FMA contraction (see build); for round-off studies."""
+    global _lib_fma
+    if _lib_fma is None:
+        _lib_fma = _bind(C.CDLL(build(contracted=True)))
+    return _lib_fma
+
+
+def _bind(L):
+    if True:
         L.orc_partition.argtypes = [C.c_int, C.c_int, _ip]
         L.orc_partition.restype = C.c_int
         L.orc_op_new.argtypes = [C.c_int, C.c_int, _dp, C.c_int, C.c_double]
@@ -84,12 +110,17 @@ def lib():
         L.orc_plane_fields.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, C.c_int, _dp]
         L.orc_plane_fields.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
-        _lib = L
-    return _lib
+        L.orc_set_num_threads.argtypes = [C.c_int]
+    return L
 
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (for timing)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def partition(N: int, sub_n: int) -> np.ndarray:
@@ -188,33 +219,34 @@ def base_profile(p: dict):
 class Solver:
     """FP64 reference solver for one box.  State arrays have shape (5, nz, ny, nx)."""
 
-    def __init__(self, p: dict, thresh: float = THRESH_FP64):
+    def __init__(self, p: dict, thresh: float = THRESH_FP64, contracted: bool = False):
         self.p = dict(p)
         self._b = _box(p)
         self.shape = (5, p["n"][2], p["n"][1], p["n"][0])
-        self._s = lib().orc_solver_new(C.byref(self._b), thresh)
+        self._L = lib_contracted() if contracted else lib()
+        self._s = self._L.orc_solver_new(C.byref(self._b), thresh)
         if not self._s:
             raise ValueError("box too small")
 
     def __del__(self):
         if getattr(self, "_s", None):
-            lib().orc_solver_free(self._s)
+            self._L.orc_solver_free(self._s)
             self._s = None
 
     def initial_state(self):
         Q = np.zeros(self.shape)
-        lib().orc_initial_state(self._s, Q)
+        self._L.orc_initial_state(self._s, Q)
         return Q
 
     def rhs(self, Q):
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         R = np.zeros_like(Q)
-        lib().orc_rhs(self._s, Q, R)
+        self._L.orc_rhs(self._s, Q, R)
         return R
 
     def wall_bc(self, Q):
         Q = np.array(Q, dtype=np.float64, order="C")
-        lib().orc_apply_wall_bc(self._s, Q)
+        self._L.orc_apply_wall_bc(self._s, Q)
         return Q
 
     @staticmethod
@@ -225,27 +257,27 @@ class Solver:
 
     def filter(self, Q):
         Q = np.array(Q, dtype=np.float64, order="C")
-        lib().orc_filter(self._s, Q)
+        self._L.orc_filter(self._s, Q)
         return Q
 
     def step(self, Q, nsteps: int = 1):
         """Advance a copy of Q by nsteps RK4 steps (filter on its cadence)."""
         Q = np.array(Q, dtype=np.float64, order="C")
-        lib().orc_rk_steps(self._s, Q, int(nsteps))
+        self._L.orc_rk_steps(self._s, Q, int(nsteps))
         return Q
 
     @property
     def step_count(self) -> int:
-        return lib().orc_solver_step(self._s)
+        return self._L.orc_solver_step(self._s)
 
     @step_count.setter
     def step_count(self, v: int):
-        lib().orc_solver_set_step(self._s, int(v))
+        self._L.orc_solver_set_step(self._s, int(v))
 
     def diagnostics(self, Q):
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         out = np.zeros(9)
-        lib().orc_diagnostics(self._s, Q, out)
+        self._L.orc_diagnostics(self._s, Q, out)
         return dict(mass=out[0], momentum=out[1:4].copy(), energy_total=out[4], max_speed=out[5],
                     max_dp=out[6], max_mach=out[7], nonfinite=int(out[8]))
 
@@ -257,7 +289,7 @@ class Solver:
         n = self.p["n"]
         a, b = [d for d in range(3) if d != axis]
         out = np.zeros((9 if what else 1, n[b], n[a]))
-        k = lib().orc_plane_fields(self._s, Q, axis, index, what, out)
+        k = self._L.orc_plane_fields(self._s, Q, axis, index, what, out)
         if k < 0:
             raise ValueError("bad plane request")
         return out[0] if what == 0 else out

@@ -933,3 +933,14 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops from now on (n >= 1); for timing the oracle on
+ * one core beside all of them.  Changes no arithmetic. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -331,11 +331,12 @@ def run_deriv_microbench(args):
     return 0
 
 
-def batched_run(N, steps, warmup):
+def batched_run(N, steps, warmup, mode=0):
     """64 independent boxes (edges from {32, 48, 64, 96, 128}, heights 1-2x,
     temperature contrasts 50-250 K), mixed precision, sub-domain lengths chosen
     by the autotuner, advanced together: every RK step is one CUDA-graph launch
-    whose branches are the boxes.  Returns (points, ms, init_s, tuned)."""
+    whose branches are the boxes (mode 0) or one persistent kernel over all of
+    them (mode 1).  Returns (points, ms, init_s, tuned)."""
     import torch
     import nopcs_synth as S
     boxes = S.uneven_boxes(64, seed=11)
@@ -346,6 +347,8 @@ def batched_run(N, steps, warmup):
     ctx = N.nopcs_init(boxes, prec=N.NOPCS_MIXED, stream=st.cuda_stream)
     init_s = time.perf_counter() - t0
     npts = sum(b["n"][0] * b["n"][1] * b["n"][2] for b in boxes)
+    if mode:
+        N.nopcs_set_launch(ctx, mode)
     N.nopcs_rk_step(ctx, warmup)
     N.nopcs_synchronize(ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -368,14 +371,18 @@ def run_batched(args):
     B.build()
     from paper_2203_00879_gb300 import nopcs as N
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    npts, ms, init_s, tuned = batched_run(N, args.steps, args.warmup)
+    npts, ms, init_s, tuned = batched_run(N, args.steps, args.warmup, 1)
+    _, ms_g, _, _ = batched_run(N, args.steps, args.warmup, 0)
     line = {"metric": "RK-stage grid-point updates/s, 64 uneven boxes batched (mixed)",
             "value": npts * 4 * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
             "config": {"workload": "64 uneven two-temperature boxes, edges 32-128, heights 1-2x edge, "
                                    "dT 50-250 K, seed 11", "points": npts, "init_s": init_s,
-                       "tuned_sub_n": tuned, "launch": "one CUDA graph per step, one branch per box"}}
+                       "tuned_sub_n": tuned, "launch": "one persistent kernel per step",
+                       "graph_launch": {"value": npts * 4 * args.steps / (ms_g * 1e-3),
+                                        "ms_per_step": ms_g / args.steps,
+                                        "launch": "one CUDA graph per step, one branch per box"}}}
     print(json.dumps(line))
     return 0
 
@@ -616,11 +623,15 @@ def main():
         deriv = {"grid": [512] * 3, "metric": "NOHAP first derivative of one field, ms per call", "steps": 10,
                  "hbm_peak_gbs": pk["hbm"], "tf32_peak_tflops": pk["tf32_peak"],
                  "bf16_peak_tflops": pk["bf16_peak"], "best": deriv_summary(rows)}
-        bn, bms, binit, btuned = batched_run(N, 20, 3)
+        bn, bms, binit, btuned = batched_run(N, 20, 3, 1)
+        _, bms_g, _, _ = batched_run(N, 20, 3, 0)
         batched = {"value": world * bn * 4 * 20 / (bms * 1e-3), "unit": UNIT, "points": bn, "steps": 20,
                    "ms_per_step": bms / 20, "init_s": binit, "tuned_sub_n": btuned,
+                   "launch": "one persistent kernel per step (all boxes, device work list)",
+                   "graph_launch": {"value": world * bn * 4 * 20 / (bms_g * 1e-3), "ms_per_step": bms_g / 20,
+                                    "launch": "one CUDA graph per step, one branch per box"},
                    "workload": "64 uneven two-temperature boxes, edges 32-128, heights 1-2x edge, dT 50-250 K, "
-                               "seed 11; one CUDA graph per step, one branch per box"}
+                               "seed 11"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -235,6 +235,27 @@ nopcs_status nopcs_derivative2_noalloc(nopcs_ctx *ctx, int box, int axis, int dt
 nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps);
 
 /*
+ * How nopcs_rk_step launches a step of the context's boxes (profiling off):
+ *   NOPCS_LAUNCH_GRAPH (default): one CUDA graph per step, captured at the
+ *     first step, one branch per box;
+ *   NOPCS_LAUNCH_PERSISTENT: one persistent kernel per step that runs every
+ *     box's phases (flux sweeps, viscous/source/RK stage, walls) from a device
+ *     work list, each phase of a box after the box's previous phase, every
+ *     wait bounded by wait_limit_s; results are identical to the graph's;
+ *   NOPCS_LAUNCH_PERSISTENT_WITHHOLD: as PERSISTENT, but box 0's first
+ *     dependency is never satisfied -- for testing the bounded wait: the
+ *     kernel gives up after wait_limit_s and returns, nopcs_synchronize
+ *     returns NOPCS_ETIMEOUT, and the boxes' states are undefined (reset or
+ *     set them before stepping again).
+ * The persistent modes need every box in NOPCS_MIXED with visc_compact = 0
+ * (else NOPCS_EUNSUPPORTED).  The paper has no counterpart: it runs one box
+ * per MPI job.  Errors: EINVAL (mode, wait_limit_s not in (0, 3600]),
+ * EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+enum { NOPCS_LAUNCH_GRAPH = 0, NOPCS_LAUNCH_PERSISTENT = 1, NOPCS_LAUNCH_PERSISTENT_WITHHOLD = 2 };
+nopcs_status nopcs_set_launch(nopcs_ctx *ctx, int mode, double wait_limit_s);
+
+/*
  * Evaluate the right-hand side of Eq. ge17 for the FP64 state `q` (device, 5
  * fields) of box `box` into `r` (device, 5 fields, FP64 under NOPCS_FP64 and
  * FP32 under NOPCS_MIXED), with exactly the arithmetic one RK stage uses.  The

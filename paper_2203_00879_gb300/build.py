@@ -13,6 +13,8 @@ LIB = os.path.join(HERE, "libnopcs.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# per-file nvcc flags (none at present)
+PER_FILE_FLAGS = {}
 
 
 def sources():
@@ -37,7 +39,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         src, obj = pair
         if not force and not _stale(obj, [src] + headers):
             return ""
-        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *PER_FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -63,11 +65,11 @@ if __name__ == "__main__":
     print(LIB)
 
 
+_LINE = ["line_kernels.cu", "line_body.cuh", "line_solve.cuh"]
 KERNEL_FILES = {
-    "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu"], "diagnostics": ["rk_kernels.cu"],
-    "sweep_x": ["line_kernels.cu", "line_solve.cuh"], "sweep_y": ["line_kernels.cu", "line_solve.cuh"],
-    "sweep_z": ["line_kernels.cu", "line_solve.cuh"],
-    "filter": ["line_kernels.cu", "line_solve.cuh", "rk_kernels.cu"], "visc_rk_update": ["visc_kernel.cu"],
+    "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu", "wall_body.cuh"], "diagnostics": ["rk_kernels.cu"],
+    "sweep_x": _LINE, "sweep_y": _LINE, "sweep_z": _LINE,
+    "filter": _LINE + ["rk_kernels.cu"], "visc_rk_update": ["visc_kernel.cu", "visc_body.cuh"],
 }
 
 

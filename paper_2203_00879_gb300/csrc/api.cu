@@ -110,6 +110,9 @@ struct nopcs_ctx {
     size_t pool_used = 0;
     double prof_ms[NOPCS_NUM_KERNELS] = {};
     long long prof_n[NOPCS_NUM_KERNELS] = {};
+    int launch_mode = NOPCS_LAUNCH_GRAPH;  // nopcs_set_launch
+    double wait_s = 2.0;                   // bound of the batched kernel's waits
+    BatchPlan *plan = nullptr;             // persistent launch: work list
 };
 
 namespace {
@@ -876,6 +879,7 @@ void nopcs_destroy(nopcs_ctx *ctx)
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
+    batch_plan_free(ctx->plan);
     for (auto &b : ctx->boxes) free_box(b);
     if (ctx->dev_err) dev_free(ctx->dev_err);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -989,7 +993,7 @@ nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps)
     if (s0 != NOPCS_OK) return s0;
     if (nsteps < 0) return fail(ctx, NOPCS_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return NOPCS_OK;
-    if (!ctx->profiling && !ctx->step_exec) {
+    if (!ctx->profiling && !ctx->step_exec && ctx->launch_mode == NOPCS_LAUNCH_GRAPH) {
         // capture one step of every box once, replayed for every later step;
         // each box's stage chain is its own branch of the graph (the boxes are
         // independent), so the GPU runs small boxes side by side
@@ -1031,6 +1035,10 @@ nopcs_status nopcs_rk_step(nopcs_ctx *ctx, int nsteps)
     for (int it = 0; it < nsteps; ++it) {
         if (ctx->profiling) {
             for (auto &b : ctx->boxes) CK(enqueue_step(ctx, b, ctx->stream), "rk step");
+        } else if (ctx->launch_mode != NOPCS_LAUNCH_GRAPH) {
+            CK(batch_launch(ctx->plan, ctx->dev_err, ctx->wait_s, ctx->launch_mode == NOPCS_LAUNCH_PERSISTENT_WITHHOLD,
+                            ctx->stream),
+               "persistent step");
         } else {
             CK(cudaGraphLaunch(ctx->step_exec, ctx->stream), "graph launch");
         }
@@ -1129,8 +1137,49 @@ nopcs_status nopcs_synchronize(nopcs_ctx *ctx)
     CK(cudaMemcpy(&flag, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "synchronize");
     if (flag) {
         CK(cudaMemset(ctx->dev_err, 0, sizeof(int)), "synchronize");
-        return fail(ctx, NOPCS_ETIMEOUT, "a bounded wait for the tensor cores gave up");
+        return fail(ctx, NOPCS_ETIMEOUT,
+                    flag == 2 ? "a bounded wait of the persistent step kernel gave up (the box states are undefined)"
+                              : "a bounded wait for the tensor cores gave up");
     }
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_set_launch(nopcs_ctx *ctx, int mode, double wait_limit_s)
+{
+    nopcs_status s0 = check_ctx(ctx);
+    if (s0 != NOPCS_OK) return s0;
+    if (mode < NOPCS_LAUNCH_GRAPH || mode > NOPCS_LAUNCH_PERSISTENT_WITHHOLD)
+        return fail(ctx, NOPCS_EINVAL, "mode must be NOPCS_LAUNCH_GRAPH, _PERSISTENT or _PERSISTENT_WITHHOLD");
+    if (!(wait_limit_s > 0.0) || wait_limit_s > 3600.0)
+        return fail(ctx, NOPCS_EINVAL, "wait_limit_s must be in (0, 3600]");
+    if (mode != NOPCS_LAUNCH_GRAPH && !ctx->plan) {
+        std::vector<BatchBoxIn> in;
+        for (auto &b : ctx->boxes) {
+            if (!b.mixed || b.d.visc_compact)
+                return fail(ctx, NOPCS_EUNSUPPORTED,
+                            "the persistent launch runs mixed-precision boxes with the explicit viscous terms");
+            BatchBoxIn x;
+            x.bx = b.dev;
+            for (int a = 0; a < 3; ++a) {
+                x.op[a] = b.dop32[a].dev;
+                x.lines[a] = b.lines[a];
+            }
+            x.W[0] = b.Wm(0);
+            x.W[1] = b.Wm(1);
+            x.R = b.Rm();
+            x.K = b.Km();
+            x.Dn = b.Dn();
+            x.Qn = b.Qn();
+            in.push_back(x);
+        }
+        LedgerScope scope(&ctx->ledger);
+        std::string msg;
+        const cudaError_t e = batch_plan_build(in, &ctx->plan, msg);
+        if (e != cudaSuccess)
+            return msg.empty() ? cuda_fail(ctx, e, "persistent launch plan") : fail(ctx, NOPCS_EUNSUPPORTED, msg);
+    }
+    ctx->launch_mode = mode;
+    ctx->wait_s = wait_limit_s;
     return NOPCS_OK;
 }
 

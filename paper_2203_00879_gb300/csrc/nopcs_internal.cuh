@@ -81,6 +81,8 @@ cudaError_t launch_band_field(const BandBuf &op, int axis, const int n[3], const
 struct LineOpDev {
     int N, nsub, nexp, maxm, max_tile, max_taps, max_win;
     int kconv64, kconv32;
+    int ncoef;          // end-row taps in the coef tables
+    int xpitch[2][4];   // whole-line x sweep: line pitch for 1 / 5 fields and 1..4 lines per block
     double cpL, invL;  // limits of the Thomas factors
     double alpha;
     double rb[4];
@@ -175,16 +177,17 @@ struct BoxDev {
 // them (a run resumed from nopcs_set_state continues bit for bit).
 __device__ __forceinline__ void prim_from_deviation(float rho_b, float gm1, const float D[5], float Wv[6])
 {
-    const float ir = __fdividef(1.0f, rho_b + D[0]);
-    const float u = D[1] * ir, v = D[2] * ir, w = D[3] * ir;
-    const float ke = 0.5f * (D[1] * u + D[2] * v + D[3] * w);
-    const float pd = gm1 * (D[4] - ke);
+    // fixed-order arithmetic (no contraction left to the compiler)
+    const float ir = __fdividef(1.0f, __fadd_rn(rho_b, D[0]));
+    const float u = __fmul_rn(D[1], ir), v = __fmul_rn(D[2], ir), w = __fmul_rn(D[3], ir);
+    const float ke = __fmul_rn(0.5f, __fmaf_rn(D[3], w, __fmaf_rn(D[2], v, __fmul_rn(D[1], u))));
+    const float pd = __fmul_rn(gm1, __fadd_rn(D[4], -ke));
     Wv[0] = D[0];
     Wv[1] = u;
     Wv[2] = v;
     Wv[3] = w;
     Wv[4] = pd;
-    Wv[5] = D[4] + pd;
+    Wv[5] = __fadd_rn(D[4], pd);
 }
 
 // ---- launchers (line_kernels.cu) -------------------------------------------
@@ -279,6 +282,24 @@ int diag_blocks(long long np);
 // cudaErrorMemoryAllocation, which the entry points report as NOPCS_ENOMEM.
 cudaError_t dev_alloc(void **p, size_t bytes);
 void dev_free(void *p);
+
+// ---- one persistent launch per RK step (batch_kernel.cu) -------------------------
+// One mixed-form box as the batched kernel sees it: its constants, FP32
+// derivative operators, flux-sweep tile widths (0: default) and registers.
+struct BatchBoxIn {
+    BoxDev bx;
+    LineOpDev op[3];
+    int lines[3];
+    float *W[2], *R, *K, *Dn;
+    double *Qn;
+};
+struct BatchPlan;  // device work list and launch geometry
+cudaError_t batch_plan_build(const std::vector<BatchBoxIn> &boxes, BatchPlan **plan, std::string &msg);
+// one RK step of every box; err: the context's error word (2 when a bounded
+// wait gave up); withhold: test mode, box 0's first dependency never completes
+cudaError_t batch_launch(BatchPlan *plan, int *err, double wait_s, int withhold, cudaStream_t st);
+void batch_plan_free(BatchPlan *plan);
+int batch_plan_items(const BatchPlan *plan);
 
 // ---- context access for entry points outside api.cu ------------------------
 // Validates a derivative request on box `box` (the context's device current,

@@ -509,6 +509,46 @@ cudaError_t LineOpBuf::upload()
     dev.max_taps = h.max_taps;
     dev.kconv64 = h.kconv64;
     dev.kconv32 = h.kconv32;
+    dev.ncoef = (int)h.coef.size();
+    // Whole-line x sweep (line_kernels.cu): a block holds L lines of 1 or 5
+    // fields, [field][line][row] with one pad word per 32 rows, and thread c
+    // solves sub-domain c % nsub of line (c / nsub) % L, field c / (nsub L).
+    // Pick, from 32 candidates, the line pitch that puts the first rows of a
+    // warp's columns in the fewest shared-memory bank collisions.
+    {
+        auto xrow = [](int g) { return g + (g >> 5); };
+        const int base = xrow(h.N - 1) + 1;
+        for (int fi = 0; fi < 2; ++fi) {
+            const int nf = fi ? 5 : 1;
+            for (int L = 1; L <= 4; ++L) {
+                const int cols = h.nsub * nf * L;
+                int best = base, best_score = 1 << 30;
+                for (int d = 0; d < 32; ++d) {
+                    const int ls = base + d;
+                    int score = 0;
+                    for (int w = 0; w * 32 < cols; ++w) {
+                        for (int k : {0, 17}) {
+                            int cnt[32] = {0};
+                            int mx = 0;
+                            for (int c = 32 * w; c < cols && c < 32 * w + 32; ++c) {
+                                const int b = c % h.nsub, l = (c / h.nsub) % L, f = c / (h.nsub * L);
+                                const int sb = h.sub[(size_t)b * SUB_REC];
+                                const long long addr = (long long)f * L * ls + (long long)l * ls + xrow(sb + k);
+                                const int bank = (int)(addr % 32);
+                                if (++cnt[bank] > mx) mx = cnt[bank];
+                            }
+                            score += mx;
+                        }
+                    }
+                    if (score < best_score) {
+                        best_score = score;
+                        best = ls;
+                    }
+                }
+                dev.xpitch[fi][L - 1] = best;
+            }
+        }
+    }
     dev.cpL = h.cp.back();
     dev.invL = h.inv.back();
     dev.alpha = h.alpha;

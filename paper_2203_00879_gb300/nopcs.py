@@ -57,6 +57,7 @@ _L.nopcs_get_state.argtypes = [_vp, _i, _vp]
 _L.nopcs_reset_state.argtypes = [_vp, _i]
 _L.nopcs_set_step.argtypes = [_vp, _i, C.c_longlong]
 _L.nopcs_set_memory_limit.argtypes = [C.c_ulonglong]
+_L.nopcs_set_launch.argtypes = [_vp, _i, _d]
 _L.nopcs_derivative.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp, _vp]
 _L.nopcs_derivative2_noalloc.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp]
 _L.nopcs_rk_step.argtypes = [_vp, _i]
@@ -85,7 +86,8 @@ _L.nopcs_slab_line_apply.argtypes = [_i, _i, _d, _i, _i, C.c_void_p, C.c_void_p,
 for _name in ("nopcs_slab_create", "nopcs_slab_extent", "nopcs_slab_derivative", "nopcs_slab_line_apply"):
     getattr(_L, _name).restype = _i
 for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_plane_fields", "nopcs_init", "nopcs_set_state",
-              "nopcs_get_state", "nopcs_reset_state", "nopcs_set_step", "nopcs_set_memory_limit", "nopcs_derivative",
+              "nopcs_get_state", "nopcs_reset_state", "nopcs_set_step", "nopcs_set_memory_limit", "nopcs_set_launch",
+              "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
               "nopcs_set_profiling", "nopcs_profile_read", "nopcs_operator_rows", "nopcs_box_info"):
@@ -152,6 +154,14 @@ def nopcs_set_memory_limit(nbytes: int) -> None:
     """Process-wide cap on the device bytes of each context created
     afterwards (0: no cap)."""
     _check(None, _L.nopcs_set_memory_limit(nbytes))
+
+
+NOPCS_LAUNCH_GRAPH, NOPCS_LAUNCH_PERSISTENT, NOPCS_LAUNCH_PERSISTENT_WITHHOLD = 0, 1, 2
+
+
+def nopcs_set_launch(ctx, mode: int, wait_limit_s: float = 2.0) -> None:
+    """CUDA graph per step (default) or one persistent kernel per step."""
+    _check(ctx, _L.nopcs_set_launch(ctx, mode, float(wait_limit_s)))
 
 
 def nopcs_derivative(ctx, box: int, axis: int, order: int, dtype: int, f_ptr: int, df_ptr: int,

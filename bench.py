@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024, help="grid points per axis")
+    ap.add_argument("--shape", default=None,
+                    help="nx,ny,nz of the timed box instead of n^3 (profiling small cases of one kernel)")
     ap.add_argument("--sub-n", type=int, default=64)
     ap.add_argument("--fp64-n", type=int, default=1024, help="grid of the FP64-form comparison (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -436,8 +438,13 @@ def main():
     stream = torch.cuda.current_stream()
     st = stream.cuda_stream
     n, K, W = args.n, args.steps, args.warmup
-    npts = float(n) ** 3
-    p = box(n, args.sub_n, seed=1 + rank)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (n, n, n)
+    npts = float(shape[0]) * shape[1] * shape[2]
+    if args.shape:
+        import nopcs_synth as S
+        p = S.box_params(shape, sub_n=(args.sub_n,) * 3, seed=1 + rank)
+    else:
+        p = box(n, args.sub_n, seed=1 + rank)
     ctx = N.nopcs_init([p], prec=N.NOPCS_MIXED, stream=st)
     tile_lines = N.nopcs_box_info(ctx, 0)["tile_lines"]
     N.nopcs_rk_step(ctx, W)
@@ -648,8 +655,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": workload_name(n, args.sub_n),
-                       "grid": [n, n, n], "sub_n": args.sub_n, "precision": "mixed", "form": "thomas",
+            "config": {"workload": workload_name(n, args.sub_n) if not args.shape else
+                       workload_name(n, args.sub_n).replace("%d^3" % n, "x".join(map(str, shape))),
+                       "grid": list(shape), "sub_n": args.sub_n, "precision": "mixed", "form": "thomas",
                        "sweep_tile_lines": tile_lines, "launch": "CUDA graph replay, one graph per RK4 step",
                        "filters_in_window": filters_in_window,
                        "l2": "inputs larger than L2 (FP64 state %.1f GB)" % (40 * npts / 1e9),

@@ -113,19 +113,19 @@ __device__ __noinline__ void run_sweep_x(const LineOpDev &op, const LineArgs<flo
                                          int nt, int xline)
 {
     if (xline)
-        xline_body<float, MODE_FLUX>(op, la, v, sm);
+        xline_body<float, MODE_FLUX>(op, la, v);
     else
-        line_body<float, MODE_FLUX, 0>(op, la, v, sm, nt);
+        line_body<float, MODE_FLUX, 0>(op, la, v, nt);
 }
 __device__ __noinline__ void run_sweep_y(const LineOpDev &op, const LineArgs<float> &la, int v, unsigned char *sm,
                                          int nt)
 {
-    line_body<float, MODE_FLUX, 1>(op, la, v, sm, nt);
+    line_body<float, MODE_FLUX, 1>(op, la, v, nt);
 }
 __device__ __noinline__ void run_sweep_z(const LineOpDev &op, const LineArgs<float> &la, int v, unsigned char *sm,
                                          int nt)
 {
-    line_body<float, MODE_FLUX, 2>(op, la, v, sm, nt);
+    line_body<float, MODE_FLUX, 2>(op, la, v, nt);
 }
 // the viscous stage kernel in the same specialisation as the stand-alone
 // launch (per stage, gravity along z) or the generic one

@@ -33,15 +33,19 @@ struct LineArgs {
 };
 
 // One block of the sub-domain sweep: block `vblock` of the launch grid
-// (sub-domain vblock % nsub of line tile vblock / nsub), shared memory at
-// smraw, threads 0 .. NT-1 working (a larger block's other threads only take
-// part in the barriers, so the arithmetic, and its rounding, is that of an
-// NT-thread launch).
-template <typename T, int MODE, int AXIS>
-__device__ __forceinline__ void line_body(const LineOpDev &op, const LineArgs<T> &a, const int vblock,
-                                          unsigned char *smraw, const int NT)
+// (sub-domain vblock % nsub of line tile vblock / nsub), in the block's
+// dynamic shared memory, threads 0 .. NT-1 working (a larger block's other
+// threads only take part in the barriers, so the arithmetic, and its
+// rounding, is that of an NT-thread launch).  The shared array is declared
+// here rather than passed in.
+template <typename T, int MODE, int AXIS, bool ALL = false>
+__device__ __forceinline__ void line_body(const LineOpDev &op, const LineArgs<T> &a, const unsigned vblock,
+                                          const int nt_req)
 {
-    const bool worker = (int)threadIdx.x < NT;
+    extern __shared__ __align__(32) unsigned char smraw[];
+    // ALL: every thread of the block works (the stand-alone launch)
+    const int NT = ALL ? (int)blockDim.x : nt_req;
+    const bool worker = ALL || (int)threadIdx.x < NT;
     constexpr bool SINGLE = MODE == MODE_FIELD || MODE == MODE_FIELD2;  // one field in, one out
     constexpr bool VISC = MODE == MODE_VGRAD || MODE == MODE_VDIV;      // four fields out
     constexpr int NF = SINGLE ? 1 : (VISC ? 4 : 5);
@@ -70,8 +74,10 @@ __device__ __forceinline__ void line_body(const LineOpDev &op, const LineArgs<T>
     T *sm = part + (size_t)RG * 2 * NF * LINES;
     const int nx = a.n[0], ny = a.n[1];
 
-    const int b = vblock % op.nsub;
-    const int tile = vblock / op.nsub;
+    // unsigned block index: the compiler then knows the tile coordinates are
+    // non-negative (with a signed index the z sweep ran 5% slower)
+    const int b = vblock % (unsigned)op.nsub;
+    const int tile = vblock / (unsigned)op.nsub;
     const int ta = tile % a.ntile_a;
     const int cc = tile / a.ntile_a;
     const int a0 = ta * LINES;
@@ -348,11 +354,12 @@ __device__ __forceinline__ void line_body(const LineOpDev &op, const LineArgs<T>
 // sub-domains, which from global memory would touch a cache line each.
 __host__ __device__ __forceinline__ int xrow(int g) { return g + (g >> 5); }
 
-// One block of the whole-line x sweep: lines vblock * LINES .. + LINES - 1.
+// One block of the whole-line x sweep: lines vblock * LINES .. + LINES - 1,
+// in the block's dynamic shared memory.
 template <typename T, int MODE>
-__device__ __forceinline__ void xline_body(const LineOpDev &op, const LineArgs<T> &a, const int vblock,
-                                           unsigned char *smraw)
+__device__ __forceinline__ void xline_body(const LineOpDev &op, const LineArgs<T> &a, const int vblock)
 {
+    extern __shared__ __align__(32) unsigned char smraw[];
     constexpr bool SINGLE = MODE == MODE_FIELD;
     constexpr int NF = SINGLE ? 1 : 5;
     constexpr int NIN = SINGLE ? 1 : 6;
@@ -640,5 +647,13 @@ bool line_grid(const LineOpDev &op, LineArgs<T> &a, int pref_lines, int threads_
              sizeof(T);
     return g.smem <= 227 * 1024;
 }
+
+// The whole-line x flux kernel lives in its own translation unit
+// (xline_kernels.cu).
+template <typename T>
+cudaError_t launch_xline_flux(const LineOpDev &op, const LineArgs<T> &a, long long nblk, int threads, size_t smem,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t init_xline_flux();
 
 }  // namespace nopcs

@@ -30,15 +30,7 @@ namespace nopcs {
 template <typename T, int MODE, int AXIS>
 __global__ void line_kernel(const LineOpDev op, const LineArgs<T> a)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    line_body<T, MODE, AXIS>(op, a, (int)blockIdx.x, smraw, (int)blockDim.x);
-}
-
-template <typename T, int MODE>
-__global__ void xline_kernel(const LineOpDev op, const LineArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    xline_body<T, MODE>(op, a, (int)blockIdx.x, smraw);
+    line_body<T, MODE, AXIS, true>(op, a, blockIdx.x, 0);
 }
 
 namespace {
@@ -50,10 +42,7 @@ cudaError_t launch_axis(const LineOpDev &op, LineArgs<T> a, int pref_lines, cuda
     if (!line_grid<T, MODE, AXIS>(op, a, pref_lines, 0, XLINE_MAX_LINES, g)) return cudaErrorInvalidConfiguration;
     if (g.nblk <= 0) return cudaSuccess;
     if constexpr (AXIS == 0 && MODE == MODE_FLUX) {
-        if (g.xline) {
-            xline_kernel<T, MODE><<<(unsigned)g.nblk, g.threads, g.smem, st>>>(op, a);
-            return cudaGetLastError();
-        }
+        if (g.xline) return launch_xline_flux<T>(op, a, g.nblk, g.threads, g.smem, st);
     }
     line_kernel<T, MODE, AXIS><<<(unsigned)g.nblk, g.threads, g.smem, st>>>(op, a);
     return cudaGetLastError();
@@ -76,9 +65,7 @@ cudaError_t allow_smem()
     cudaError_t e = cudaFuncSetAttribute(line_kernel<T, MODE, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if constexpr (AXIS == 0 && MODE == MODE_FLUX) {
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(xline_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)XLINE_SMEM);
+        if (e == cudaSuccess) e = init_xline_flux<T>();
     }
     return e;
 }

@@ -479,14 +479,14 @@ __device__ __forceinline__ void source_and_stage(const VArgs<T> &a, int p, int k
 
 
 template <typename T, bool EDGE, class S>
-__device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const int bx, const int by, const int bz,
-                                             unsigned char *smraw)
+__device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned bx, const unsigned by,
+                                             const unsigned bz, unsigned char *smraw)
 {
     const int stage = st_of<S>(a), ga = ga_of<S>(a);
     using V = V4<T>;
     constexpr int EW = TX + 2, FH = TY + 2;  // E_v row width, F_v rows (one-node halos)
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
-    const int xs = bx * TX, ys = by * TY;
+    const int xs = bx * TX, ys = by * TY;  // unsigned block coordinates, as blockIdx
     Ring<T> rg;
     rg.s = reinterpret_cast<V *>(smraw);
     rg.x0 = min(xs, max(nx - TX, 0));
@@ -696,8 +696,8 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const int bx, co
 // blocks whose x and y ranges (with the one-node flux halo) stay off the walls
 // take the branch-free stencils.
 template <typename T, class S = RunSpec>
-__device__ __forceinline__ void visc_rk_block(const VArgs<T> &a, const int bx, const int by, const int bz,
-                                              unsigned char *smraw)
+__device__ __forceinline__ void visc_rk_block(const VArgs<T> &a, const unsigned bx, const unsigned by,
+                                              const unsigned bz, unsigned char *smraw)
 {
     const int nx = a.n[0], ny = a.n[1];
     const int x0 = min(bx * TX, max(nx - TX, 0)), y0 = min(by * TY, max(ny - TY, 0));

@@ -36,7 +36,7 @@ template <typename T, class S>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) visc_rk_kernel(const VArgs<T> a)
 {
     extern __shared__ __align__(32) unsigned char smraw[];
-    visc_rk_block<T, S>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, smraw);
+    visc_rk_block<T, S>(a, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
 }
 
 // Compact viscous terms, step 2 of 3: the nodal viscous fluxes from the

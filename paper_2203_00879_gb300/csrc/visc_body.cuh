@@ -19,6 +19,13 @@ constexpr int PX = TX + 2 * HALO, PY = TY + 2 * HALO, PLANE = PX * PY;
 constexpr int RING = 5;   // planes o-2 .. o+2 (o-3 .. o+1 / o-1 .. o+3 at a wall)
 constexpr int NPF = 4;    // u, v, w, T
 constexpr int GSLOTS = 3; // planes of G_v kept
+// FP32: E_v and F_v of plane o+1 are evaluated with its G_v, from one stencil,
+// and kept for the next plane (two slots); FP64 evaluates them at plane o (one
+// slot), which keeps its shared memory within two blocks per SM.
+template <typename T>
+__host__ __device__ constexpr bool flux_ahead() { return sizeof(T) == 4; }
+template <typename T>
+__host__ __device__ constexpr int ef_slots() { return flux_ahead<T>() ? 2 : 1; }
 
 // Every field array is passed as its own base pointer, so a node's address is
 // one 32-bit index away from a kernel parameter (boxes hold < 2^31 points).
@@ -491,9 +498,11 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
     rg.s = reinterpret_cast<V *>(smraw);
     rg.x0 = min(xs, max(nx - TX, 0));
     rg.y0 = min(ys, max(ny - TY, 0));
-    V *EV = rg.s + (size_t)RING * PLANE;  // [TY][EW], local x + 1
-    V *FV = EV + TY * EW;                 // [FH][TX], local y + 1
-    V *GV = FV + FH * TX;                 // [GSLOTS][TY][TX]
+    constexpr bool AHEAD = flux_ahead<T>();
+    constexpr int EFS = ef_slots<T>();
+    V *EV = rg.s + (size_t)RING * PLANE;  // [EFS][TY][EW], local x + 1
+    V *FV = EV + EFS * TY * EW;           // [EFS][FH][TX], local y + 1
+    V *GV = FV + EFS * FH * TX;           // [GSLOTS][TY][TX]
     const int z0 = bz * a.zc, z1 = min(nz, z0 + a.zc);
     const int tx = (int)(threadIdx.x % TX), ty = (int)(threadIdx.x / TX);
     const int x = rg.x0 + tx, y = rg.y0 + ty;
@@ -502,8 +511,9 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
     const bool in_dom = !EDGE || (x < nx && y < ny);
     const bool own = !EDGE || (in_dom && x >= xs && y >= ys);
     // G_v planes are computed in increasing order; ghi is the last one, and
-    // the ring holds the GSLOTS planes up to it
-    int ghi = -1000;
+    // the ring holds the GSLOTS planes up to it; efhi is the last plane whose
+    // E_v and F_v are held (plane j in slot j mod EFS)
+    int ghi = -1000, efhi = -1000;
 
     // ring bases of planes o-3 .. o+3, refreshed once per plane (plane o + d
     // sits in slot (o + d) mod RING; o+-3 share the slots of o-+2, and a
@@ -523,20 +533,20 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
     // stencil at local (lx, ly) of plane j = o + dz, |dz| <= 2 (planes outside
     // the box are never dereferenced: the z mode picks the one-sided form)
     auto stencil_at = [&](int lx, int ly, int dz, int j) {
-        Stencil<T, EDGE> S;
-        S.b0 = pbase(dz + 3);
-        S.bm1 = pbase(dz + 2);
-        S.bp1 = pbase(dz + 4);
-        S.bm2 = pbase(dz >= -1 ? dz + 1 : dz + 3);
-        S.bp2 = pbase(dz <= 1 ? dz + 5 : dz + 3);
-        S.off = (ly + HALO) * PX + (lx + HALO);
-        S.xm = EDGE ? wall_mode(rg.x0 + lx, nx) : 0;
-        S.ym = EDGE ? wall_mode(rg.y0 + ly, ny) : 0;
-        S.zm = wall_mode(j, nz);
-        S.ihx = a.ih2[0];
-        S.ihy = a.ih2[1];
-        S.ihz = a.ih2[2];
-        return S;
+        Stencil<T, EDGE> St;
+        St.b0 = pbase(dz + 3);
+        St.bm1 = pbase(dz + 2);
+        St.bp1 = pbase(dz + 4);
+        St.bm2 = pbase(dz >= -1 ? dz + 1 : dz + 3);
+        St.bp2 = pbase(dz <= 1 ? dz + 5 : dz + 3);
+        St.off = (ly + HALO) * PX + (lx + HALO);
+        St.xm = EDGE ? wall_mode(rg.x0 + lx, nx) : 0;
+        St.ym = EDGE ? wall_mode(rg.y0 + ly, ny) : 0;
+        St.zm = wall_mode(j, nz);
+        St.ihx = a.ih2[0];
+        St.ihy = a.ih2[1];
+        St.ihz = a.ih2[2];
+        return St;
     };
 
     PlaneLoad<T, S> pl;
@@ -568,60 +578,73 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
             pb6 = sb(3);
         }
         // ---- 1. nodal viscous fluxes ------------------------------------------
-        if (in_dom) {
-            const Stencil<T, EDGE> S = stencil_at(tx, ty, 0, o);
-            const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
-            const ViscK<T> k(a, q.w);
-            EV[ty * EW + tx + 1] = flux_E(k, q, gx, gy, gz, S.xm == 0);
-            FV[(ty + 1) * TX + tx] = flux_F(k, q, gx, gy, gz, S.ym == 0);
-        }
-        // halo fluxes (the same arithmetic as in the tile that owns the node,
-        // so the same bits): F_v on the y halo in warps 0-1, E_v on the x halo
-        // in warp 2, so no warp evaluates more than one halo flux per plane
-        if (threadIdx.x < 2 * TX) {  // F_v on the y halo
-            const int t = threadIdx.x;
-            const int side = t / TX, hx = t % TX;
-            const int ly = side ? TY : -1;
-            const int gxx = rg.x0 + hx, gyy = rg.y0 + ly;
-            if (!EDGE || (gyy >= 0 && gyy < ny && gxx < nx)) {
-                const Stencil<T, EDGE> S = stencil_at(hx, ly, 0, o);
-                const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
-                FV[(ly + 1) * TX + hx] = flux_F(ViscK<T>(a, q.w), q, gx, gy, gz, S.ym == 0);
+        // fluxes_at(dz, wantEF, wantG): the requested fluxes of plane j = o + dz
+        // at this thread's node from one stencil; with wantEF also F_v on the
+        // y halo (warps 0-1) and E_v on the x halo (warp 2), with the same
+        // arithmetic as in the tile that owns the node, so the same bits, and
+        // no warp evaluating more than one halo flux per plane
+        auto fluxes_at = [&](const int dz, const bool wantEF, const bool wantG) {
+            const int j = o + dz;
+            const int es = j & (EFS - 1);
+            V *ev = EV + es * TY * EW, *fv = FV + es * FH * TX;
+            if (in_dom) {
+                const Stencil<T, EDGE> St = stencil_at(tx, ty, dz, j);
+                const V q = St.val(), gx = St.dx(), gy = St.dy(), gz = St.dz();
+                const ViscK<T> k(a, q.w);
+                if (wantEF) {
+                    ev[ty * EW + tx + 1] = flux_E(k, q, gx, gy, gz, St.xm == 0);
+                    fv[(ty + 1) * TX + tx] = flux_F(k, q, gx, gy, gz, St.ym == 0);
+                }
+                if (wantG) GV[((j % GSLOTS) * TY + ty) * TX + tx] = flux_G(k, q, gx, gy, gz, St.zm == 0);
             }
-        } else if (threadIdx.x < 2 * TX + 2 * TY) {  // E_v on the x halo
-            const int t = threadIdx.x - 2 * TX;
-            const int side = t / TY, hy = t % TY;
-            const int lx = side ? TX : -1;
-            const int gxx = rg.x0 + lx, gyy = rg.y0 + hy;
-            if (!EDGE || (gxx >= 0 && gxx < nx && gyy < ny)) {
-                const Stencil<T, EDGE> S = stencil_at(lx, hy, 0, o);
-                const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
-                EV[hy * EW + lx + 1] = flux_E(ViscK<T>(a, q.w), q, gx, gy, gz, S.xm == 0);
+            if (!wantEF) return;
+            if (threadIdx.x < 2 * TX) {  // F_v on the y halo
+                const int t = threadIdx.x;
+                const int side = t / TX, hx = t % TX;
+                const int ly = side ? TY : -1;
+                const int gxx = rg.x0 + hx, gyy = rg.y0 + ly;
+                if (!EDGE || (gyy >= 0 && gyy < ny && gxx < nx)) {
+                    const Stencil<T, EDGE> St = stencil_at(hx, ly, dz, j);
+                    const V q = St.val(), gx = St.dx(), gy = St.dy(), gz = St.dz();
+                    fv[(ly + 1) * TX + hx] = flux_F(ViscK<T>(a, q.w), q, gx, gy, gz, St.ym == 0);
+                }
+            } else if (threadIdx.x < 2 * TX + 2 * TY) {  // E_v on the x halo
+                const int t = threadIdx.x - 2 * TX;
+                const int side = t / TY, hy = t % TY;
+                const int lx = side ? TX : -1;
+                const int gxx = rg.x0 + lx, gyy = rg.y0 + hy;
+                if (!EDGE || (gxx >= 0 && gxx < nx && gyy < ny)) {
+                    const Stencil<T, EDGE> St = stencil_at(lx, hy, dz, j);
+                    const V q = St.val(), gx = St.dx(), gy = St.dy(), gz = St.dz();
+                    ev[hy * EW + lx + 1] = flux_E(ViscK<T>(a, q.w), q, gx, gy, gz, St.xm == 0);
+                }
             }
-        }
-        // G_v planes the z divergence of plane o needs: o-1 and o+1, or
-        // o..o+2 / o-2..o on a wall; all of jlo..jlo+2 once computed
+        };
+        // the divergence of plane o needs E_v, F_v of plane o and G_v of o-1 and
+        // o+1, or of o..o+2 / o-2..o on a z wall: all of jlo..jlo+2
         const int zw = wall_mode(o, nz);
         const int jlo = zw == 1 ? o : (zw == 2 ? o - 2 : o - 1);
-        if (zw == 0 && ghi == o) {
-            // steady state away from the z walls: the one new plane o + 1,
-            // with its plane offset known at compile time
-            const int j = o + 1, slot = j % GSLOTS;
-            ghi = j;
-            if (in_dom) {
-                const Stencil<T, EDGE> S = stencil_at(tx, ty, 1, j);
-                const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
-                GV[(slot * TY + ty) * TX + tx] = flux_G(ViscK<T>(a, q.w), q, gx, gy, gz, S.zm == 0);
+        if (zw == 0 && ghi == o && (!AHEAD || efhi == o)) {
+            // steady state away from the z walls, plane offsets known at compile
+            // time: all three fluxes of plane o+1 (FP64: E_v, F_v of plane o and
+            // G_v of plane o+1)
+            if constexpr (AHEAD) {
+                fluxes_at(1, true, true);
+                efhi = o + 1;
+            } else {
+                fluxes_at(0, true, false);
+                fluxes_at(1, false, true);
+                efhi = o;
             }
+            ghi = o + 1;
         } else {
-            for (int j = max(ghi + 1, jlo); j <= jlo + 2; ++j) {
-                const int slot = j % GSLOTS;
-                ghi = j;
-                if (in_dom) {
-                    const Stencil<T, EDGE> S = stencil_at(tx, ty, j - o, j);
-                    const V q = S.val(), gx = S.dx(), gy = S.dy(), gz = S.dz();
-                    GV[(slot * TY + ty) * TX + tx] = flux_G(ViscK<T>(a, q.w), q, gx, gy, gz, S.zm == 0);
-                }
+            for (int j = jlo; j <= jlo + 2; ++j) {
+                const bool wantG = j > ghi;
+                const bool wantEF = j > efhi && (j == o || (AHEAD && j == o + 1));
+                if (!wantG && !wantEF) continue;
+                fluxes_at(j - o, wantEF, wantG);
+                if (wantG) ghi = j;
+                if (wantEF) efhi = j;
             }
         }
         __syncthreads();
@@ -650,8 +673,9 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
             }
             const int xm = EDGE ? wall_mode(x, nx) : 0, ym = EDGE ? wall_mode(y, ny) : 0;
             const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
-            const V *e = EV + ty * EW + tx + 1;
-            const V *f = FV + (ty + 1) * TX + tx;
+            const int es = o & (EFS - 1);
+            const V *e = EV + es * TY * EW + ty * EW + tx + 1;
+            const V *f = FV + es * FH * TX + (ty + 1) * TX + tx;
             V dvx, dvy, dvz;
             if (xm == 0)
                 dvx = d_central(e[1], e[-1], ihx);
@@ -711,7 +735,8 @@ __device__ __forceinline__ void visc_rk_block(const VArgs<T> &a, const unsigned 
 template <typename T>
 size_t ring_bytes()
 {
-    return ((size_t)RING * NPF * PLANE + 4 * TY * (TX + 2) + 4 * (TY + 2) * TX + (size_t)GSLOTS * 4 * TY * TX) *
+    return ((size_t)RING * NPF * PLANE + ef_slots<T>() * (4 * TY * (TX + 2) + 4 * (TY + 2) * TX) +
+            (size_t)GSLOTS * 4 * TY * TX) *
            sizeof(T);
 }
 

@@ -68,7 +68,7 @@ if __name__ == "__main__":
 _LINE = ["line_kernels.cu", "line_body.cuh", "line_solve.cuh"]
 KERNEL_FILES = {
     "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu", "wall_body.cuh"], "diagnostics": ["rk_kernels.cu"],
-    "sweep_x": _LINE, "sweep_y": _LINE, "sweep_z": _LINE,
+    "sweep_x": _LINE + ["xline_kernels.cu"], "sweep_y": _LINE, "sweep_z": _LINE,
     "filter": _LINE + ["rk_kernels.cu"], "visc_rk_update": ["visc_kernel.cu", "visc_body.cuh"],
 }
 

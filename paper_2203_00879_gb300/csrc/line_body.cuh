@@ -354,6 +354,29 @@ __device__ __forceinline__ void line_body(const LineOpDev &op, const LineArgs<T>
 // sub-domains, which from global memory would touch a cache line each.
 __host__ __device__ __forceinline__ int xrow(int g) { return g + (g >> 5); }
 
+// Inviscid flux along x (Eq. ge3) of one point's stage primitives
+// v = (rho - rho_b, u, v, w, p, H - H_b) into the tile rows d[k FS], k = 0..4;
+// gk is the point's coordinate along gravity.
+template <typename T>
+__device__ __forceinline__ void xline_flux_point(const LineArgs<T> &a, T *d, const size_t FS, const T v[6],
+                                                 const int gk)
+{
+    const T rho = a.b0[gk] + v[0];
+    const T uu = v[1], vv = v[2], ww = v[3], pp = v[4];
+    const T H = a.b1[gk] + v[5];
+    const T m = rho * uu;
+    d[0] = m;
+    d[FS] = m * uu + pp;
+    d[2 * FS] = m * vv;
+    d[3 * FS] = m * ww;
+    d[4 * FS] = H * uu;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void xline_solve_store(const LineOpDev &op, const LineArgs<T> &a, T *sm,
+                                                  const T *ctab, const T *tcp, const T *tiv, const int line0,
+                                                  const int nl);
+
 // One block of the whole-line x sweep: lines vblock * LINES .. + LINES - 1,
 // in the block's dynamic shared memory.
 template <typename T, int MODE>
@@ -364,7 +387,6 @@ __device__ __forceinline__ void xline_body(const LineOpDev &op, const LineArgs<T
     constexpr int NF = SINGLE ? 1 : 5;
     constexpr int NIN = SINGLE ? 1 : 6;
     constexpr int U = 4;     // staged points in flight per thread and field
-    constexpr int NEXP = 2;  // explicit rows at each wall (derivative)
     const int N = op.N;      // = nx
     const int nx = a.n[0], ny = a.n[1];
     const int LINES = a.lines, LS = a.rt;  // lines per block, line pitch (padded)
@@ -407,23 +429,32 @@ __device__ __forceinline__ void xline_body(const LineOpDev &op, const LineArgs<T
                 if constexpr (SINGLE) {
                     d[0] = v[u][0];
                 } else {
-                    // inviscid flux along x (Eq. ge3) of the stage primitives
-                    const int gk = a.ga == 0 ? g : gl;
-                    const T rho = a.b0[gk] + v[u][0];
-                    const T uu = v[u][1], vv = v[u][2], ww = v[u][3], pp = v[u][4];
-                    const T H = a.b1[gk] + v[u][5];
-                    const T m = rho * uu;
-                    d[0] = m;
-                    d[FS] = m * uu + pp;
-                    d[2 * FS] = m * vv;
-                    d[3 * FS] = m * ww;
-                    d[4 * FS] = H * uu;
+                    xline_flux_point(a, d, FS, v[u], a.ga == 0 ? g : gl);
                 }
             }
         }
     }
     __syncthreads();
-    // ---- columns: thread c solves sub-domain c % nsub of line (c / nsub) % nl, field c / (nsub nl)
+    xline_solve_store<T, MODE>(op, a, sm, ctab, tcp, tiv, line0, nl);
+}
+
+// The solve and the store of the whole-line x sweep, once lines line0 ..
+// line0 + nl - 1 are staged in the tile sm (and a barrier has passed): the
+// columns, thread c solving sub-domain c % nsub of line (c / nsub) % nl, field
+// c / (nsub nl), in phases A-C, then the rows scaled by 1/h into the outputs.
+template <typename T, int MODE>
+__device__ __forceinline__ void xline_solve_store(const LineOpDev &op, const LineArgs<T> &a, T *sm,
+                                                  const T *ctab, const T *tcp, const T *tiv, const int line0,
+                                                  const int nl)
+{
+    constexpr bool SINGLE = MODE == MODE_FIELD;
+    constexpr int NF = SINGLE ? 1 : 5;
+    constexpr int NEXP = 2;  // explicit rows at each wall (derivative)
+    const int N = op.N;      // = nx
+    const int nx = a.n[0];
+    const int LINES = a.lines, LS = a.rt;
+    const size_t FS = (size_t)LINES * LS;
+    const int KC = sizeof(T) == 8 ? op.kconv64 : op.kconv32;
     const int nsub = op.nsub;
     const int c = threadIdx.x;
     const bool active = c < nsub * NF * nl;

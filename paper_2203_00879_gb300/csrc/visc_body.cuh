@@ -647,20 +647,15 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
                 if (wantEF) efhi = j;
             }
         }
-        __syncthreads();
-        // ---- 2. divergence, source, RK stage; next plane's primitives ----------
-        const int zn = lhi + 1;
-        const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
-        if (next) pl.issue(a, zn);
-        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) pl.prefetch(a, zn + 1);  // the next issue's plane
-        if (own && o + 1 < z1) prefetch_node<T, S>(a, x + nx * (y + ny * (o + 1)));
+        // the node's own inputs of phase 2, loaded before the barrier so that
+        // they are in flight while the block waits at it
+        const int p = x + nx * (y + ny * o);
+        T r[5], w0 = T(0);
+        float kd[5], dn[5];
         if (own) {
-            const int p = x + nx * (y + ny * o);
-            T r[5];
-            float kd[5], dn[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) r[k] = a.R[k][p];
-            const T w0 = a.W[0][p];
+            w0 = a.W[0][p];
             if constexpr (sizeof(T) == 4) {
                 if (stage >= 2) {
 #pragma unroll
@@ -671,6 +666,15 @@ __device__ __forceinline__ void visc_rk_body(const VArgs<T> &a, const unsigned b
                     for (int k = 0; k < 5; ++k) dn[k] = a.Dn[k][p];
                 }
             }
+        }
+        __syncthreads();
+        // ---- 2. divergence, source, RK stage; next plane's primitives ----------
+        const int zn = lhi + 1;
+        const bool next = o + 1 < z1 && zn < nz && zn <= o + 3;
+        if (next) pl.issue(a, zn);
+        if (next && zn + 1 < nz && zn + 1 <= o + 4 && o + 2 < z1) pl.prefetch(a, zn + 1);  // the next issue's plane
+        if (own && o + 1 < z1) prefetch_node<T, S>(a, x + nx * (y + ny * (o + 1)));
+        if (own) {
             const int xm = EDGE ? wall_mode(x, nx) : 0, ym = EDGE ? wall_mode(y, ny) : 0;
             const T ihx = a.ih2[0], ihy = a.ih2[1], ihz = a.ih2[2];
             const int es = o & (EFS - 1);

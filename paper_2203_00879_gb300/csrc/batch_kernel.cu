@@ -147,7 +147,7 @@ __device__ __forceinline__ void run_visc_any(const VArgs<float> &va, int bx, int
     run_visc<RunSpec>(va, bx, by, bz, sm);
 }
 
-__global__ void __launch_bounds__(BT, 2) batch_step_kernel(const BParams p)
+__global__ void __launch_bounds__(BT, 3) batch_step_kernel(const BParams p)
 {
     extern __shared__ __align__(32) unsigned char smraw[];
     __shared__ int s_item, s_go;

@@ -151,6 +151,14 @@ __global__ void __launch_bounds__(BT, 3) batch_step_kernel(const BParams p)
 {
     extern __shared__ __align__(32) unsigned char smraw[];
     __shared__ int s_item, s_go;
+    // the item's arguments, copied from the device box table: the phase code
+    // then reads its pointers and constants from shared memory instead of
+    // through global loads ahead of every data access
+    constexpr int ARGW = (int)((sizeof(VArgs<float>) > sizeof(LineOpDev) + sizeof(LineArgs<float>)
+                                    ? sizeof(VArgs<float>)
+                                    : sizeof(LineOpDev) + sizeof(LineArgs<float>)) /
+                               8);
+    __shared__ unsigned long long s_args[ARGW];
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(p.next, 1);
         __syncthreads();
@@ -182,13 +190,30 @@ __global__ void __launch_bounds__(BT, 3) batch_step_kernel(const BParams p)
         __syncthreads();
         if (s_go) {
             const BStage &S = B.st[it.stage];
+            LineOpDev *sop = reinterpret_cast<LineOpDev *>(s_args);
+            LineArgs<float> *sla = reinterpret_cast<LineArgs<float> *>(s_args + sizeof(LineOpDev) / 8);
+            VArgs<float> *sva = reinterpret_cast<VArgs<float> *>(s_args);
+            {
+                auto copy = [&](void *dst, const void *src, int bytes) {
+                    const unsigned long long *a = (const unsigned long long *)src;
+                    unsigned long long *b = (unsigned long long *)dst;
+                    for (int k = threadIdx.x; k < bytes / 8; k += BT) b[k] = a[k];
+                };
+                if (it.phase <= PH_SZ) {
+                    copy(sop, &B.op[it.phase], (int)sizeof(LineOpDev));
+                    copy(sla, &S.la[it.phase], (int)sizeof(LineArgs<float>));
+                } else if (it.phase == PH_VISC) {
+                    copy(sva, &S.va, (int)sizeof(VArgs<float>));
+                }
+                __syncthreads();
+            }
             const int last = min(it.first + B.chunk[it.phase], B.ntile[it.phase]);
             for (int v = it.first; v < last; ++v) {
                 switch (it.phase) {
-                case PH_SX: run_sweep_x(B.op[0], S.la[0], v, smraw, B.nt[0], B.xline); break;
-                case PH_SY: run_sweep_y(B.op[1], S.la[1], v, smraw, B.nt[1]); break;
-                case PH_SZ: run_sweep_z(B.op[2], S.la[2], v, smraw, B.nt[2]); break;
-                case PH_VISC: run_visc_any(S.va, v % B.gx, (v / B.gx) % B.gy, v / (B.gx * B.gy), smraw); break;
+                case PH_SX: run_sweep_x(*sop, *sla, v, smraw, B.nt[0], B.xline); break;
+                case PH_SY: run_sweep_y(*sop, *sla, v, smraw, B.nt[1]); break;
+                case PH_SZ: run_sweep_z(*sop, *sla, v, smraw, B.nt[2]); break;
+                case PH_VISC: run_visc_any(*sva, v % B.gx, (v / B.gx) % B.gy, v / (B.gx * B.gy), smraw); break;
                 case PH_FACE: {
                     const long long tot = face_count(B.bx);
                     const long long t1 = min(tot, (long long)(v + 1) * FACE_CHUNK);

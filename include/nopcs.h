@@ -166,6 +166,33 @@ const char *nopcs_last_error(const nopcs_ctx *ctx);
 nopcs_status nopcs_set_state(nopcs_ctx *ctx, int box, const double *q);
 nopcs_status nopcs_get_state(nopcs_ctx *ctx, int box, double *q);
 
+/*
+ * Staged state upload, for callers that stream a sequence of states through a
+ * box (ensemble members, restarts): the copy of the next state overlaps the
+ * work on the current one.  The paper has no counterpart.
+ *
+ * nopcs_stage_state enqueues the copy of a state (5 FP64 fields, np each, the
+ * layout of nopcs_set_state; host memory -- pinned for full speed -- or device
+ * memory) into the box's staging buffer on the context's copy stream and
+ * returns without waiting.  The copy starts once the previous commit of the
+ * box has read the staging buffer.  `q` must stay valid and unchanged until
+ * the state has been committed and a later nopcs_diagnostics or
+ * nopcs_synchronize call has returned.
+ *
+ * nopcs_commit_state makes the staged state the box's current state, ordered
+ * on the context stream after the work already enqueued there: the stream
+ * waits for the staging copy, the staged state replaces Q_n (a device copy)
+ * and the derived fields are refreshed, as nopcs_set_state does.  It returns
+ * without waiting; the step counter is unchanged.
+ *
+ * The staging buffer (5 np doubles) is allocated by the first
+ * nopcs_stage_state of a box and counted against nopcs_set_memory_limit; it is
+ * freed with the context.  Errors: EINVAL (bad box, q NULL, a commit with no
+ * staged state), ENOMEM (the staging buffer), ECUDA.
+ */
+nopcs_status nopcs_stage_state(nopcs_ctx *ctx, int box, const double *q);
+nopcs_status nopcs_commit_state(nopcs_ctx *ctx, int box);
+
 /* Reset box `box` to its initial state and its step counter to 0. */
 nopcs_status nopcs_reset_state(nopcs_ctx *ctx, int box);
 

@@ -74,6 +74,10 @@ struct BoxRes {
     void *base = nullptr;
     double *partial = nullptr, *diag_out = nullptr;
     void *scratch = nullptr;  // order-2 derivative intermediate (lazy)
+    double *stage = nullptr;  // nopcs_stage_state: staged state, 5 np doubles (lazy)
+    cudaEvent_t staged_ev = nullptr;     // the staging copy is done
+    cudaEvent_t committed_ev = nullptr;  // the last commit has read the staged state
+    bool staged = false;
     int nblk_diag = 0;
     long long step = 0;
     double *Qn() const { return Q; }
@@ -113,6 +117,7 @@ struct nopcs_ctx {
     int launch_mode = NOPCS_LAUNCH_GRAPH;  // nopcs_set_launch
     double wait_s = 2.0;                   // bound of the batched kernel's waits
     BatchPlan *plan = nullptr;             // persistent launch: work list
+    cudaStream_t copy_stream = nullptr;    // nopcs_stage_state's copies (lazy)
 };
 
 namespace {
@@ -218,6 +223,12 @@ void free_box(BoxRes &b)
     if (b.base) dev_free(b.base);
     if (b.partial) dev_free(b.partial);
     if (b.scratch) dev_free(b.scratch);
+    if (b.stage) dev_free(b.stage);
+    if (b.staged_ev) cudaEventDestroy(b.staged_ev);
+    if (b.committed_ev) cudaEventDestroy(b.committed_ev);
+    b.stage = nullptr;
+    b.staged_ev = b.committed_ev = nullptr;
+    b.staged = false;
     b.Q = nullptr;
     b.W = b.R = b.Gv = b.base = b.scratch = nullptr;
     b.partial = b.diag_out = nullptr;
@@ -872,6 +883,7 @@ void nopcs_destroy(nopcs_ctx *ctx)
     if (cur != ctx->device) cudaSetDevice(ctx->device);
     LedgerScope scope(&ctx->ledger);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
     for (auto st : ctx->branch) cudaStreamDestroy(st);
     for (auto ev : ctx->branch_ev) cudaEventDestroy(ev);
@@ -882,6 +894,10 @@ void nopcs_destroy(nopcs_ctx *ctx)
     batch_plan_free(ctx->plan);
     for (auto &b : ctx->boxes) free_box(b);
     if (ctx->dev_err) dev_free(ctx->dev_err);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     const int dev = ctx->device;
     delete ctx;
@@ -904,6 +920,48 @@ nopcs_status nopcs_set_state(nopcs_ctx *ctx, int box, const double *q)
        "set_state");
     CK(refresh_mixed(b, ctx->stream), "set_state");
     CK(cudaStreamSynchronize(ctx->stream), "set_state");
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_stage_state(nopcs_ctx *ctx, int box, const double *q)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    if (!q) return fail(ctx, NOPCS_EINVAL, "q is NULL");
+    BoxRes &b = ctx->boxes[box];
+    const size_t bytes = 5 * (size_t)b.dev.np * sizeof(double);
+    if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "stage_state");
+    if (!b.staged_ev) CK(cudaEventCreateWithFlags(&b.staged_ev, cudaEventDisableTiming), "stage_state");
+    if (!b.committed_ev) {
+        CK(cudaEventCreateWithFlags(&b.committed_ev, cudaEventDisableTiming), "stage_state");
+        // nothing has read the buffer yet: the first wait below passes at once
+        CK(cudaEventRecord(b.committed_ev, ctx->copy_stream), "stage_state");
+    }
+    if (!b.stage) {
+        LedgerScope scope(&ctx->ledger);
+        CK(dev_alloc((void **)&b.stage, bytes), "stage_state");
+    }
+    // the previous commit must have copied the staged state out first
+    CK(cudaStreamWaitEvent(ctx->copy_stream, b.committed_ev, 0), "stage_state");
+    CK(cudaMemcpyAsync(b.stage, q, bytes, cudaMemcpyDefault, ctx->copy_stream), "stage_state");
+    CK(cudaEventRecord(b.staged_ev, ctx->copy_stream), "stage_state");
+    b.staged = true;
+    return NOPCS_OK;
+}
+
+nopcs_status nopcs_commit_state(nopcs_ctx *ctx, int box)
+{
+    nopcs_status s = check_box(ctx, box);
+    if (s != NOPCS_OK) return s;
+    BoxRes &b = ctx->boxes[box];
+    if (!b.staged) return fail(ctx, NOPCS_EINVAL, "no state is staged for this box");
+    CK(cudaStreamWaitEvent(ctx->stream, b.staged_ev, 0), "commit_state");
+    CK(cudaMemcpyAsync(b.Qn(), b.stage, 5 * (size_t)b.dev.np * sizeof(double), cudaMemcpyDeviceToDevice,
+                       ctx->stream),
+       "commit_state");
+    CK(cudaEventRecord(b.committed_ev, ctx->stream), "commit_state");
+    CK(refresh_mixed(b, ctx->stream), "commit_state");
+    b.staged = false;
     return NOPCS_OK;
 }
 

@@ -186,7 +186,8 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
     const double gm1 = bx.gamma - 1.0, igam = 1.0 / bx.gamma;
     // maxima of |V|^2 and Mach^2 are kept and their square roots taken once
     // in the final kernel (the square root is monotone); one FP64 division
-    // for 1/rho and one for Mach^2 = |V|^2 rho / (gamma p) per point
+    // for 1/rho per point, and one for Mach^2 = |V|^2 rho / (gamma p) only
+    // where it can raise the maximum
     double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
         const int y = rw % ny, z = rw / ny;
@@ -208,7 +209,14 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
             const double pr = gm1 * (E - 0.5 * r * s2);
             v[5] = fmax(v[5], s2);
             v[6] = fmax(v[6], fabs(pr - bx.p_h64[kg]));
-            v[7] = fmax(v[7], s2 * r * igam / pr);
+            // Mach^2 = num / pr can raise the maximum only where num exceeds
+            // v7 pr (for pr > 0; the factor 0.999999 keeps every point whose
+            // rounded quotient could exceed v7).  Elsewhere the quotient is at
+            // most v7, or not a number, and the maximum stays as it is, so the
+            // division -- the costly FP64 operation here -- runs only where it
+            // can matter, and the result is the same.
+            const double num = s2 * r * igam;
+            if (num > v[7] * pr * 0.999999) v[7] = fmax(v[7], num / pr);
         }
     }
     for (int k = 0; k < DIAG_REC; ++k) sh[k][threadIdx.x] = v[k];

@@ -54,6 +54,8 @@ _L.nopcs_last_error.argtypes = [_vp]
 _L.nopcs_last_error.restype = C.c_char_p
 _L.nopcs_set_state.argtypes = [_vp, _i, _vp]
 _L.nopcs_get_state.argtypes = [_vp, _i, _vp]
+_L.nopcs_stage_state.argtypes = [_vp, _i, _vp]
+_L.nopcs_commit_state.argtypes = [_vp, _i]
 _L.nopcs_reset_state.argtypes = [_vp, _i]
 _L.nopcs_set_step.argtypes = [_vp, _i, C.c_longlong]
 _L.nopcs_set_memory_limit.argtypes = [C.c_ulonglong]
@@ -86,7 +88,7 @@ _L.nopcs_slab_line_apply.argtypes = [_i, _i, _d, _i, _i, C.c_void_p, C.c_void_p,
 for _name in ("nopcs_slab_create", "nopcs_slab_extent", "nopcs_slab_derivative", "nopcs_slab_line_apply"):
     getattr(_L, _name).restype = _i
 for _name in ("nopcs_operator_apply", "nopcs_band_apply", "nopcs_plane_fields", "nopcs_init", "nopcs_set_state",
-              "nopcs_get_state", "nopcs_reset_state", "nopcs_set_step", "nopcs_set_memory_limit", "nopcs_set_launch",
+              "nopcs_get_state", "nopcs_stage_state", "nopcs_commit_state", "nopcs_reset_state", "nopcs_set_step", "nopcs_set_memory_limit", "nopcs_set_launch",
               "nopcs_derivative",
               "nopcs_derivative2_noalloc",
               "nopcs_rk_step", "nopcs_rhs", "nopcs_filter", "nopcs_diagnostics", "nopcs_synchronize",
@@ -140,6 +142,14 @@ def nopcs_set_state(ctx, box: int, q_ptr: int) -> None:
 
 def nopcs_get_state(ctx, box: int, q_ptr: int) -> None:
     _check(ctx, _L.nopcs_get_state(ctx, box, q_ptr))
+
+
+def nopcs_stage_state(ctx, box: int, q_ptr: int) -> None:
+    _check(ctx, _L.nopcs_stage_state(ctx, box, q_ptr))
+
+
+def nopcs_commit_state(ctx, box: int) -> None:
+    _check(ctx, _L.nopcs_commit_state(ctx, box))
 
 
 def nopcs_reset_state(ctx, box: int) -> None:

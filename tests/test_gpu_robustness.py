@@ -158,3 +158,53 @@ def test_initial_state_draws_the_published_splitmix_vector():
     V = [Q[c + 1, k, j, i] / Q[0, k, j, i] for c in range(3)] + \
         [Q[c + 1, k, j, i + 1] / Q[0, k, j, i + 1] for c in range(2)]
     np.testing.assert_allclose(V, expected_velocity(amp), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_staged_state_equals_set_state(prec):
+    """nopcs_stage_state + nopcs_commit_state give the state nopcs_set_state
+    gives, bit for bit, from pinned host memory: a state staged while a step
+    runs does not reach that step, and becomes current only at its commit."""
+    import torch
+    N = binding()
+    p = S.box_params((30, 28, 26), sub_n=(12, 12, 12), perturb_amp=1e-3, seed=9)
+    ctx = N.nopcs_init([p], prec=prec, stream=stream_ptr())
+    try:
+        N.nopcs_rk_step(ctx, 2)
+        QA = _state(N, ctx, p)
+        N.nopcs_rk_step(ctx, 3)
+        QB = _state(N, ctx, p)
+        hA = torch.from_numpy(QA.copy()).pin_memory()
+        hB = torch.from_numpy(QB.copy()).pin_memory()
+        # reference: set_state(A), one step
+        N.nopcs_set_state(ctx, 0, hA.data_ptr())
+        N.nopcs_rk_step(ctx, 1)
+        ref1 = _state(N, ctx, p)
+        # staged: A staged and committed; B staged while the step on A runs
+        N.nopcs_stage_state(ctx, 0, hA.data_ptr())
+        N.nopcs_commit_state(ctx, 0)
+        N.nopcs_stage_state(ctx, 0, hB.data_ptr())
+        N.nopcs_rk_step(ctx, 1)
+        got1 = _state(N, ctx, p)
+        N.nopcs_commit_state(ctx, 0)
+        gotB = _state(N, ctx, p)
+        # a commit needs a staged state
+        with pytest.raises(N.NopcsError) as ei:
+            N.nopcs_commit_state(ctx, 0)
+        assert ei.value.status == N.NOPCS_EINVAL
+        with pytest.raises(N.NopcsError) as ei:
+            N.nopcs_stage_state(ctx, 0, 0)
+        assert ei.value.status == N.NOPCS_EINVAL
+        # the derived fields were refreshed too: stepping from the committed B
+        # equals stepping from set_state(B)
+        N.nopcs_rk_step(ctx, 1)
+        gotB1 = _state(N, ctx, p)
+        N.nopcs_set_state(ctx, 0, hB.data_ptr())
+        N.nopcs_rk_step(ctx, 1)
+        refB1 = _state(N, ctx, p)
+    finally:
+        N.nopcs_destroy(ctx)
+    assert np.array_equal(got1, ref1)
+    assert np.array_equal(gotB, QB)
+    assert np.array_equal(gotB1, refB1)
+    assert not np.array_equal(ref1, QA)

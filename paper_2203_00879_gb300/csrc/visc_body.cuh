@@ -42,6 +42,8 @@ struct VArgs {
     const T *R[5];
     int stage;
     double dt;
+    double dt6, dt3, dt2;                 // dt/6, dt/3, dt/2 (host-computed: no FP64 division per node)
+    float cdt2, cdt1;                     // FP32 dt/2 and dt (mixed-form stage states)
     T *Rout[5];                           // stage 0: right-hand side out
     double *Qn[5], *acc[5], *Qout[5];     // FP64 stage registers
     float *Kacc[5], *Dn[5];               // mixed form: slope sum, deviation of Q_n
@@ -418,11 +420,11 @@ __device__ __forceinline__ void mixed_update(const VArgs<float> &a, int p, int k
     if (s < 4) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) a.Kacc[k][p] = K[k];
-        const float c = (float)(s == 3 ? a.dt : 0.5 * a.dt);
+        const float c = s == 3 ? a.cdt1 : a.cdt2;
 #pragma unroll
         for (int k = 0; k < 5; ++k) D[k] = __fmaf_rn(c, r[k], dn[k]);
     } else {
-        const double w6 = a.dt / 6.0;
+        const double w6 = a.dt6;
         double q[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -465,8 +467,8 @@ __device__ __forceinline__ void source_and_stage(const VArgs<T> &a, int p, int k
         mixed_update<S>(a, p, kg, r, kd, dn);
     } else {
         // classical RK4: acc collects Q_n + dt (k1 + 2 k2 + 2 k3 + k4) / 6
-        const double bw = (stage == 1 || stage == 4) ? a.dt / 6.0 : a.dt / 3.0;
-        const double cw = stage == 3 ? a.dt : 0.5 * a.dt;
+        const double bw = (stage == 1 || stage == 4) ? a.dt6 : a.dt3;
+        const double cw = stage == 3 ? a.dt : a.dt2;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const double rk = (double)r[k];
@@ -775,6 +777,11 @@ VArgs<T> make_vargs(const BoxDev &bx, const T *W, const T *R, int stage, const S
     for (int k = 0; k < 5; ++k) a.R[k] = R + (size_t)k * bx.np;
     a.stage = stage;
     a.dt = bx.dt;
+    a.dt6 = bx.dt / 6.0;
+    a.dt3 = bx.dt / 3.0;
+    a.dt2 = 0.5 * bx.dt;
+    a.cdt2 = (float)(0.5 * bx.dt);
+    a.cdt1 = (float)bx.dt;
     auto fp = [&](auto *base, int k) { return base ? base + (size_t)k * bx.np : base; };
     for (int k = 0; k < 5; ++k) {
         a.Rout[k] = fp(g.Rout, k);

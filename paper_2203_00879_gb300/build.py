@@ -67,9 +67,10 @@ if __name__ == "__main__":
 
 _LINE = ["line_kernels.cu", "line_body.cuh", "line_solve.cuh"]
 KERNEL_FILES = {
-    "prep": ["rk_kernels.cu"], "wall_bc": ["rk_kernels.cu", "wall_body.cuh"], "diagnostics": ["rk_kernels.cu"],
+    "prep": ["rk_kernels.cu", "fp_bits.cuh"], "wall_bc": ["rk_kernels.cu", "wall_body.cuh", "fp_bits.cuh"],
+    "diagnostics": ["rk_kernels.cu", "fp_bits.cuh"],
     "sweep_x": _LINE + ["xline_kernels.cu"], "sweep_y": _LINE, "sweep_z": _LINE,
-    "filter": _LINE + ["rk_kernels.cu"], "visc_rk_update": ["visc_kernel.cu", "visc_body.cuh"],
+    "filter": _LINE + ["rk_kernels.cu"], "visc_rk_update": ["visc_kernel.cu", "visc_body.cuh", "fp_bits.cuh"],
 }
 
 

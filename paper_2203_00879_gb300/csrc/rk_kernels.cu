@@ -5,6 +5,7 @@
 // diagnostics reduction.
 #include <math.h>
 
+#include "fp_bits.cuh"
 #include "wall_body.cuh"
 
 namespace nopcs {
@@ -185,16 +186,25 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
     const int nx = bx.n[0], ny = bx.n[1], rows = bx.n[1] * bx.n[2];
     const double gm1 = bx.gamma - 1.0, igam = 1.0 / bx.gamma;
     // maxima of |V|^2 and Mach^2 are kept and their square roots taken once
-    // in the final kernel (the square root is monotone); one FP64 division
-    // for 1/rho per point, and one for Mach^2 = |V|^2 rho / (gamma p) only
-    // where it can raise the maximum
+    // in the final kernel (the square root is monotone).  The FP64 work per
+    // point is what decides this kernel's time (GB300 runs FP64 at 1/64 of the
+    // FP32 rate): 1/rho by two Newton steps instead of a division, the
+    // gravity-axis terms once per row where gravity is not along x, and the
+    // division for Mach^2 = |V|^2 rho / (gamma p) only where it can raise the
+    // maximum.
     double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double v7t = 0.0;  // v[7] * 0.999999
     for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
         const int y = rw % ny, z = rw / ny;
         const long long base = (long long)rw * nx;
+        // coordinate along gravity of the row (gravity along y or z)
+        const int kr = bx.ga == 1 ? y : z;
+        const double kgh_r = kr * bx.h[bx.ga];
+        const double ph_r = bx.ga != 0 ? bx.p_h64[kr] : 0.0;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const long long p = base + x;
-            const int kg = bx.ga == 0 ? x : (bx.ga == 1 ? y : z);
+            const double kgh = bx.ga == 0 ? x * bx.h[0] : kgh_r;
+            const double ph = bx.ga == 0 ? bx.p_h64[x] : ph_r;
             const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
             const bool bad = !isfinite(r) || !isfinite(mx) || !isfinite(my) || !isfinite(mz) || !isfinite(E);
             if (bad) v[8] = 1.0;
@@ -202,21 +212,22 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
             v[1] += mx;
             v[2] += my;
             v[3] += mz;
-            v[4] += E + r * bx.g * (kg * bx.h[bx.ga]);
-            const double ir = 1.0 / r;
+            v[4] += E + r * bx.g * kgh;
+            const double ir = recip_newton(r);
             const double u = mx * ir, vv = my * ir, w = mz * ir;
             const double s2 = u * u + vv * vv + w * w;
             const double pr = gm1 * (E - 0.5 * r * s2);
             v[5] = fmax(v[5], s2);
-            v[6] = fmax(v[6], fabs(pr - bx.p_h64[kg]));
+            v[6] = fmax(v[6], fabs(pr - ph));
             // Mach^2 = num / pr can raise the maximum only where num exceeds
             // v7 pr (for pr > 0; the factor 0.999999 keeps every point whose
             // rounded quotient could exceed v7).  Elsewhere the quotient is at
-            // most v7, or not a number, and the maximum stays as it is, so the
-            // division -- the costly FP64 operation here -- runs only where it
-            // can matter, and the result is the same.
+            // most v7, or not a number, and the maximum stays as it is.
             const double num = s2 * r * igam;
-            if (num > v[7] * pr * 0.999999) v[7] = fmax(v[7], num / pr);
+            if (num > v7t * pr) {
+                v[7] = fmax(v[7], num / pr);
+                v7t = v[7] * 0.999999;
+            }
         }
     }
     for (int k = 0; k < DIAG_REC; ++k) sh[k][threadIdx.x] = v[k];

@@ -8,6 +8,7 @@
 
 #include <math.h>
 
+#include "fp_bits.cuh"
 #include "nopcs_internal.cuh"
 
 namespace nopcs {
@@ -388,39 +389,6 @@ __device__ __forceinline__ V4<T> flux_G(const ViscK<T> &k, const V4<T> &q, const
 }
 
 
-// Conversions between binary32 and binary64 by integer operations on the
-// IEEE 754 bit patterns, for the FP64 update of the RK4 state, whose
-// conversions would otherwise load the FP64 pipe (GB300 runs it at 1/64 of the
-// FP32 rate).  Normal numbers only; zero, subnormals, infinities and NaN take
-// the hardware conversion, which gives the same result.
-//   widen: sign kept, exponent re-biased by 1023 - 127, the 23 fraction bits
-//          moved to the top of the 52 (exact);
-//   narrow: exponent re-biased by 127 - 1023 where the result is a normal
-//          binary32, fraction cut to 23 bits and rounded to nearest, ties to
-//          even, from the 29 bits cut off; a carry out of the fraction moves
-//          into the exponent (up to infinity), as rounding does.
-__device__ __forceinline__ double widen_f32(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e - 1u < 0xfeu) {
-        const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-        return __hiloint2double((int)hi, (int)(u << 29));
-    }
-    return (double)f;
-}
-__device__ __forceinline__ float narrow_f64(double d)
-{
-    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    const unsigned e = (hi >> 20) & 0x7ffu;
-    if (e - 897u < 254u) {
-        unsigned r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-        const unsigned rem = lo & 0x1fffffffu;
-        r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
-        return __uint_as_float(r | (hi & 0x80000000u));
-    }
-    return (float)d;
-}
 
 // primitives of a stage state from its FP32 deviation D = (rho', m_x, m_y, m_z, E')
 __device__ __forceinline__ void prim_from_dev(const VArgs<float> &a, int p, int kg, const float D[5])

@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--compact-n", type=int, default=1024,
                     help="grid of the compact-viscous-term measurement, mixed form (0: skip)")
     ap.add_argument("--compact-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-n", type=int, default=128, help="oracle sample grid for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle sample steps for the CPU baseline")
     ap.add_argument("--cpu1-n", type=int, default=64, help="oracle sample grid for the one-core timing")

@@ -206,7 +206,10 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
             const double kgh = bx.ga == 0 ? x * bx.h[0] : kgh_r;
             const double ph = bx.ga == 0 ? bx.p_h64[x] : ph_r;
             const double r = Q[p], mx = Q[np + p], my = Q[2 * np + p], mz = Q[3 * np + p], E = Q[4 * np + p];
-            const bool bad = !isfinite(r) || !isfinite(mx) || !isfinite(my) || !isfinite(mz) || !isfinite(E);
+            // not finite: exponent field all ones (infinity or NaN), tested on
+            // the high words by integer operations instead of FP64 compares
+            auto nonfinite = [](double q) { return ((unsigned)__double2hiint(q) & 0x7ff00000u) == 0x7ff00000u; };
+            const bool bad = nonfinite(r) || nonfinite(mx) || nonfinite(my) || nonfinite(mz) || nonfinite(E);
             if (bad) v[8] = 1.0;
             v[0] += r;
             v[1] += mx;

@@ -218,3 +218,31 @@ def test_staged_state_equals_set_state(prec):
     assert np.array_equal(gotB, QB)
     assert np.array_equal(gotB1, refB1)
     assert not np.array_equal(ref1, QA)
+
+
+def test_split_state_copies_are_exact():
+    """States of 64 MB and more cross the host link in four parts on four
+    streams: set_state and stage + commit of an 84 MB state (128^3) from pinned
+    host memory give back exactly the state that was sent."""
+    import torch
+    N = binding()
+    n = 128
+    p = S.box_params((n, n, n), sub_n=(64, 64, 64), perturb_amp=1e-3, seed=21)
+    ctx = N.nopcs_init([p], prec=N.NOPCS_FP64, stream=stream_ptr())
+    try:
+        Q = _state(N, ctx, p)
+        g = np.random.default_rng(3)
+        send = torch.from_numpy(Q * (1.0 + 1e-6 * g.standard_normal(Q.shape))).pin_memory()
+        assert send.numel() * 8 >= 64 << 20
+        N.nopcs_set_state(ctx, 0, send.data_ptr())
+        back1 = _state(N, ctx, p)
+        N.nopcs_reset_state(ctx, 0)
+        N.nopcs_stage_state(ctx, 0, send.data_ptr())
+        N.nopcs_commit_state(ctx, 0)
+        back2 = _state(N, ctx, p)
+    finally:
+        N.nopcs_destroy(ctx)
+    ref = send.numpy()
+    assert np.array_equal(back1, ref)
+    assert np.array_equal(back2, ref)
+    assert not np.array_equal(ref, Q)

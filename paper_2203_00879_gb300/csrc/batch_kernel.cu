@@ -32,8 +32,11 @@ namespace nopcs {
 namespace {
 
 constexpr int BT = 256;             // threads per block (the viscous tile's)
-constexpr int FACE_CHUNK = 16384;   // wall face nodes per item
-enum { PH_SX = 0, PH_SY, PH_SZ, PH_VISC, PH_FACE, PH_EDGE, NPH };
+// wall nodes per tile of the face and edge phases: four passes of a block,
+// so that a box's wall phases spread over many blocks instead of holding the
+// box's next phase behind a few long items
+constexpr int WALL_CHUNK = 4 * BT;
+enum { PH_SX = 0, PH_SY, PH_SZ, PH_VISC, PH_FACE, PH_EDGE, PH_CORNER, NPH };
 
 struct BStage {
     LineArgs<float> la[3];
@@ -216,22 +219,25 @@ __global__ void __launch_bounds__(BT, 3) batch_step_kernel(const BParams p)
                 case PH_VISC: run_visc_any(*sva, v % B.gx, (v / B.gx) % B.gy, v / (B.gx * B.gy), smraw); break;
                 case PH_FACE: {
                     const long long tot = face_count(B.bx);
-                    const long long t1 = min(tot, (long long)(v + 1) * FACE_CHUNK);
-                    for (long long t = (long long)v * FACE_CHUNK + threadIdx.x; t < t1; t += BT) {
+                    const long long t1 = min(tot, (long long)(v + 1) * WALL_CHUNK);
+                    for (long long t = (long long)v * WALL_CHUNK + threadIdx.x; t < t1; t += BT) {
                         int c[3];
                         face_node(B.bx, t, c);
                         wall_node(B.bx, c, S.Q, S.Dn, S.Wf, S.Ww);
                     }
                     break;
                 }
-                default: {  // edges, then the corners, which read them
+                case PH_EDGE: {
                     const long long tot = edge_count(B.bx);
-                    for (long long t = threadIdx.x; t < tot; t += BT) {
+                    const long long t1 = min(tot, (long long)(v + 1) * WALL_CHUNK);
+                    for (long long t = (long long)v * WALL_CHUNK + threadIdx.x; t < t1; t += BT) {
                         int c[3];
                         edge_node(B.bx, t, c);
                         wall_node(B.bx, c, S.Q, S.Dn, S.Wf, S.Ww);
                     }
-                    __syncthreads();
+                    break;
+                }
+                default: {  // the corners, which read the edges
                     if (threadIdx.x < 8) {
                         int c[3];
                         corner_node(B.bx, threadIdx.x, c);
@@ -336,8 +342,9 @@ cudaError_t batch_plan_build(const std::vector<BatchBoxIn> &in, BatchPlan **out,
         const long long nface = 2 * ((long long)(I.bx.n[1] - 2) * (I.bx.n[2] - 2) +
                                      (long long)(I.bx.n[0] - 2) * (I.bx.n[2] - 2) +
                                      (long long)(I.bx.n[0] - 2) * (I.bx.n[1] - 2));
-        B.ntile[PH_FACE] = (int)((nface + FACE_CHUNK - 1) / FACE_CHUNK);
-        B.ntile[PH_EDGE] = 1;
+        B.ntile[PH_FACE] = (int)((nface + WALL_CHUNK - 1) / WALL_CHUNK);
+        B.ntile[PH_EDGE] = (int)((edge_count(I.bx) + WALL_CHUNK - 1) / WALL_CHUNK);
+        B.ntile[PH_CORNER] = 1;
         // blocks per item: about a quarter of a GPU wave per phase of a big
         // box, single blocks for small ones
         for (int ph = 0; ph < NPH; ++ph) {

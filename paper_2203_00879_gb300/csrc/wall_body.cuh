@@ -107,7 +107,7 @@ __device__ void set_wall_node_w(const BoxDev &bx, float *W, const int c[3])
 }
 
 // face nodes: exactly one wall coordinate; node t of 2 (fx + fy + fz)
-__device__ __forceinline__ long long face_count(const BoxDev &bx)
+__host__ __device__ __forceinline__ long long face_count(const BoxDev &bx)
 {
     const long long nx = bx.n[0], ny = bx.n[1], nz = bx.n[2];
     return 2 * ((ny - 2) * (nz - 2) + (nx - 2) * (nz - 2) + (nx - 2) * (ny - 2));
@@ -144,7 +144,7 @@ __device__ __forceinline__ void face_node(const BoxDev &bx, long long t, int c[3
 // at 0 or n - 1 (4 combinations); every edge node reads only face and
 // interior nodes, so the edges run in parallel, and the corners, which read
 // edge nodes, follow
-__device__ __forceinline__ long long edge_count(const BoxDev &bx)
+__host__ __device__ __forceinline__ long long edge_count(const BoxDev &bx)
 {
     return 4LL * (bx.n[0] - 2) + 4LL * (bx.n[1] - 2) + 4LL * (bx.n[2] - 2);
 }

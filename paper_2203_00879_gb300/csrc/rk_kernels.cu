@@ -188,12 +188,22 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
     // maxima of |V|^2 and Mach^2 are kept and their square roots taken once
     // in the final kernel (the square root is monotone).  The FP64 work per
     // point is what decides this kernel's time (GB300 runs FP64 at 1/64 of the
-    // FP32 rate): 1/rho by two Newton steps instead of a division, the
-    // gravity-axis terms once per row where gravity is not along x, and the
-    // division for Mach^2 = |V|^2 rho / (gamma p) only where it can raise the
-    // maximum.
+    // FP32 rate): the sums are FP64 at every point; the maxima are evaluated
+    // in FP64 (1/rho by two Newton steps instead of a division, the Mach^2
+    // division only where it can raise the maximum) only at the points that a
+    // binary32 screen cannot rule out; the gravity-axis terms are taken once
+    // per row where gravity is not along x.
     double v[DIAG_REC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     double v7t = 0.0;  // v[7] * 0.999999
+    // FP32 screen for the maxima: a point goes through the FP64 evaluation
+    // below only if its binary32 estimates, with margins well above their
+    // rounding error, could reach the current maxima (or are not numbers);
+    // the maxima are those of the FP64 values of the points that could raise
+    // them, so they are the same as evaluating every point in FP64
+    float v5f = 0.0f, v6f = 0.0f, v7f = 0.0f;
+    bool screening = true;
+    int nseen = 0, ncand = 0;
+    const float gm1f = (float)gm1, igamf = (float)igam;
     for (int rw = blockIdx.x; rw < rows; rw += gridDim.x) {
         const int y = rw % ny, z = rw / ny;
         const long long base = (long long)rw * nx;
@@ -201,6 +211,11 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
         const int kr = bx.ga == 1 ? y : z;
         const double kgh_r = kr * bx.h[bx.ga];
         const double ph_r = bx.ga != 0 ? bx.p_h64[kr] : 0.0;
+        // screen of |p - p_h|: p - p_h = (gamma - 1)(E - E_b - kinetic) + c
+        // with c = (gamma - 1) E_b - p_h, so that the binary32 estimate resolves
+        // disturbances far smaller than p itself
+        const double Eb_r = bx.ga != 0 && bx.E_b64 ? bx.E_b64[kr] : 0.0;
+        const float cf_r = narrow_f64(gm1 * Eb_r - ph_r);
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const long long p = base + x;
             const double kgh = bx.ga == 0 ? x * bx.h[0] : kgh_r;
@@ -216,20 +231,56 @@ __global__ void diag_partial_kernel(const BoxDev bx, const double *__restrict__ 
             v[2] += my;
             v[3] += mz;
             v[4] += E + r * bx.g * kgh;
-            const double ir = recip_newton(r);
-            const double u = mx * ir, vv = my * ir, w = mz * ir;
-            const double s2 = u * u + vv * vv + w * w;
-            const double pr = gm1 * (E - 0.5 * r * s2);
-            v[5] = fmax(v[5], s2);
-            v[6] = fmax(v[6], fabs(pr - ph));
-            // Mach^2 = num / pr can raise the maximum only where num exceeds
-            // v7 pr (for pr > 0; the factor 0.999999 keeps every point whose
-            // rounded quotient could exceed v7).  Elsewhere the quotient is at
-            // most v7, or not a number, and the maximum stays as it is.
-            const double num = s2 * r * igam;
-            if (num > v7t * pr) {
-                v[7] = fmax(v[7], num / pr);
-                v7t = v[7] * 0.999999;
+            // screen: |V|^2 to ~1e-6 relative; p to tol absolute (a few
+            // binary32 ulps of |E| + |kinetic| + |p_h|, with room to spare),
+            // so Mach^2 only where p is known to 1e-4 relative
+            bool cand = true;
+            if (screening) {
+                const double Eb = bx.ga == 0 ? (bx.E_b64 ? bx.E_b64[x] : 0.0) : Eb_r;
+                const float cf = bx.ga == 0 ? narrow_f64(gm1 * Eb - ph) : cf_r;
+                const float rf = narrow_f64(r), mxf = narrow_f64(mx), myf = narrow_f64(my), mzf = narrow_f64(mz);
+                const float Ef = narrow_f64(E), phf = narrow_f64(ph), dEf = narrow_f64(E - Eb);
+                const float irf = __fdividef(1.0f, rf);
+                const float s2f = (mxf * mxf + myf * myf + mzf * mzf) * (irf * irf);
+                const float kinf = 0.5f * rf * s2f;
+                const float prf = gm1f * (Ef - kinf);
+                const float tol = 2e-6f * (fabsf(Ef) + fabsf(kinf) + fabsf(phf));
+                // the disturbance pressure to 2e-6 of its own terms, plus 1e-14
+                // of E and p_h for the rounding of the FP64 evaluation it
+                // stands for
+                const float dpf = fabsf(gm1f * (dEf - kinf) + cf);
+                const float tol_dp =
+                    2e-6f * (fabsf(dEf) + fabsf(kinf) + fabsf(cf)) + 1e-14f * (fabsf(Ef) + fabsf(phf));
+                const float machf = __fdividef(s2f * rf * igamf, prf);
+                cand = !(s2f < v5f) || !(dpf + tol_dp < v6f) || !(fabsf(prf) > 1e4f * tol) ||
+                       !(machf * 1.0003f < v7f);
+                // a state whose maxima sit at the FP64 rounding floor (a box at
+                // rest) passes every point: the thread then stops screening
+                ncand += cand ? 1 : 0;
+                if (++nseen == 256) screening = 2 * ncand < nseen;
+            }
+            if (cand) {
+                const double ir = recip_newton(r);
+                const double u = mx * ir, vv = my * ir, w = mz * ir;
+                const double s2 = u * u + vv * vv + w * w;
+                const double pr = gm1 * (E - 0.5 * r * s2);
+                v[5] = fmax(v[5], s2);
+                v[6] = fmax(v[6], fabs(pr - ph));
+                // Mach^2 = num / pr can raise the maximum only where num
+                // exceeds v7 pr (for pr > 0; the factor 0.999999 keeps every
+                // point whose rounded quotient could exceed v7).  Elsewhere the
+                // quotient is at most v7, or not a number, and the maximum
+                // stays as it is.
+                const double num = s2 * r * igam;
+                if (num > v7t * pr) {
+                    v[7] = fmax(v[7], num / pr);
+                    v7t = v[7] * 0.999999;
+                }
+                // thresholds a little below the maxima; none while a maximum is
+                // too small for the binary32 estimates to resolve
+                v5f = v[5] > 1e-30 ? narrow_f64(v[5]) * 0.99999f : 0.0f;
+                v6f = narrow_f64(v[6]) * 0.99999f;
+                v7f = v[7] > 1e-30 ? narrow_f64(v[7]) * 0.9999f : 0.0f;
             }
         }
     }
